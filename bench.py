@@ -1,0 +1,418 @@
+#!/usr/bin/env python3
+"""Benchmark of the FSBM collision-coalescence step on GB300.
+
+Metric: grid-point coal updates per second = (active grid points x collision steps) / time
+of fsbm_coal_step. One bench "step" is one fsbm_coal_step call over the whole batch: the
+compaction pass plus the persistent collision kernel advancing every active point by the
+workload's collision steps.
+
+Default workload (N = 1): the CONUS-12km-shaped domain, 425 x 300 x 50 points with 15 %
+cloudy (956,249 active points), 33 mass-doubling bins, 5 species, dt = 5 s x 10 collision
+steps per call, plain FP64 form. The spectra (1.26 GB) exceed L2, so no flush is needed
+between timed calls; the state keeps evolving from call to call, as in a model run.
+
+Besides the headline number the line carries:
+  e2e          the same metric through fsbm_coal_step_host with pinned host buffers
+               (host->device and device->host copies inside the timed region);
+  roofline     the collision kernel against the ALU roofline (pairs/s against the pipe
+               rate divided by the algorithmic pipe operations per pair);
+  cpu_baseline the CPU oracle on a bounded sample of the same points, all host cores;
+  forms        the FP32 split form on the same domain (CUDA-graph replay) and the
+               264-bin, 5-species stress points in both forms.
+
+--impl reference times the CPU oracle as the reference arm (bounded sample per step).
+Multi-GPU (torchrun): every rank runs its own seeded domain (weak scaling); the points are
+independent, so there is no collective in the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Per-SM unit counts of the GB300 SM (sm_103) used for the ALU roofline.
+SMS = 152
+FP32_LANES = 128            # FP32 FMA per clock per SM
+MUFU_LANES = 16             # special-function (lg2/ex2/rcp/rsq) results per clock per SM
+FP64_PER_CLK = 2            # FP64 FMA per clock per SM (measured 1.73 at 1.9 GHz nominal-clock model)
+# Algorithmic operations of one bin-pair interaction (one unordered pair, one step):
+#  pair flux: C = K N_i N_j dt phi (4 mul + 1 min), dM = C (x_i + x_j) (1 add 1 mul),
+#  g = M_k + dM (1 add), rho = M_{k+1} / g (1 div), x1 = ln(rho) (1 log), e^{x1/2} (1 exp),
+#  expm1(-c x1) (1 exp), F = dM * a * b / x1 (2 mul 1 div), clip (2), accumulate (3 add)
+#  plus the two loss mat-vec passes (R and the limited loss: 2 FMA per ordered pair = 4 per
+#  unordered pair, 2 when the limiter does not fire).
+FP_OPS_PER_PAIR = 18 + 4    # plain FP adds/muls/FMAs/compares (pipe: FMA or FP64)
+MUFU_OPS_PER_PAIR = 5       # 2 divides + 3 transcendentals (FP32: one MUFU op each)
+# FP64 transcendentals and divides run on the FP64 pipe as polynomial/Newton sequences;
+# the algorithmic count takes 8 FP64 ops per divide and 18 per log/exp/expm1 (range
+# reduction + degree-11 polynomial), the cost of a minimal double-precision evaluation.
+FP64_OPS_PER_PAIR = FP_OPS_PER_PAIR + 2 * 8 + 3 * 18
+
+
+def pairs_per_point(n, ns):
+    return ns * n * (n + 1) // 2 + ns * (ns - 1) // 2 * n * n
+
+
+def alu_peak_pairs(precision, sm_mhz):
+    f = sm_mhz * 1e6
+    if precision == 0:
+        return SMS * FP64_PER_CLK * f / FP64_OPS_PER_PAIR
+    return min(SMS * FP32_LANES * f / FP_OPS_PER_PAIR, SMS * MUFU_LANES * f / MUFU_OPS_PER_PAIR)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return out
+        loaded = [r for r in rows if r[2] > 250.0] or rows
+        out["sm_mhz"] = statistics.median(r[0] for r in loaded)
+        out["sm_max_mhz"] = max(r[1] for r in rows)
+        out["samples"] = len(loaded)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in loaded:
+            for name, v in zip(names, r[3][1:]):
+                if v.lower() == "active":
+                    seen.add(name)
+        out["reasons"] = sorted(seen)
+        return out
+
+
+def cpu_sample_run(w, budget_s=12.0, seed=3):
+    """Time the CPU oracle (all host cores) on a bounded random sample of active points."""
+    import oracle
+    import synth
+
+    act = np.nonzero((w.cloudy if w.cloudy is not None else np.ones(w.n_points, bool)) &
+                     (w.species_mask > 0))[0]
+    rng = np.random.default_rng(seed)
+    cores = oracle.max_threads()
+    n = min(len(act), 4 * cores)
+    elapsed, ws = 0.0, None
+    while True:
+        idx = np.sort(rng.choice(act, n, replace=False))
+        ws = synth.subset(w, idx)
+        t0 = time.perf_counter()
+        oracle.run(ws)
+        elapsed = time.perf_counter() - t0
+        if elapsed > budget_s / 4 or n >= len(act):
+            break
+        n = min(len(act), int(n * max(2.0, budget_s / max(elapsed, 1e-3) / 2)))
+    return dict(value=n * w.n_steps / elapsed, unit="grid-point coal updates/s", cores=cores, kind="oracle",
+                sample=f"{n} random active points of the same domain x {w.n_steps} steps "
+                       f"({elapsed:.1f} s, FP64 C oracle, OpenMP over points)")
+
+
+def build_workload(name, rank):
+    import synth
+
+    if name == "conus":
+        return synth.config2(seed=2001 + 1000 * rank)
+    if name == "stress":
+        return synth.config5(n_points=20_000, seed=5001 + 1000 * rank)
+    if name == "ragged":
+        return synth.config4(n_points=200_000, seed=4001 + 1000 * rank)
+    raise ValueError(name)
+
+
+def time_steps(fc, ds, w, steps, warmup, stream, torch, barrier=None):
+    for _ in range(warmup):
+        fc.step(ds, w.dt, w.n_steps)
+    torch.cuda.synchronize()
+    fc.stats()  # reset the timing totals
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fc.step(ds, w.dt, w.n_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    ms = e0.elapsed_time(e1)
+    return ms, fc.stats()
+
+
+def run_form(pkg, torch, w, precision, steps, warmup, graph=False):
+    """Time one form on one workload; returns a dict with value, kernel time and work."""
+    with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
+        ds = fc.upload(w.state(copy=False))
+        fc.set_graph(graph)
+        fc.set_timing(True)
+        ms, st = time_steps(fc, ds, w, steps, warmup, fc.stream, torch)
+    n_active = st["n_active"]
+    pairs = pairs_per_active(w)
+    out = dict(value=n_active * w.n_steps * steps / (ms / 1e3), ms_per_step=ms / steps, n_active=n_active,
+               pairs_per_s=pairs * w.n_steps * steps / (ms / 1e3))
+    if st["coal_launches"]:
+        out["coal_ms"] = st["coal_ms"] / st["coal_launches"]
+    elif st["steps_timed"]:
+        out["step_ms_graph"] = st["step_ms"] / st["steps_timed"]
+    return out
+
+
+def pairs_per_active(w):
+    """Bin pairs per collision step summed over the active points (every bin active)."""
+    act = (w.species_mask > 0)
+    if w.cloudy is not None:
+        act &= w.cloudy > 0
+    return int(w.pairs_per_step()[act].sum())
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["conus", "stress", "ragged"], default="conus")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32 and 264-bin side measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import torch
+    import paper_2409_07232_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    precision = pkg.FSBM_FP64 if args.precision == "fp64" else pkg.FSBM_FP32_SPLIT
+    w = build_workload(args.workload, rank)
+    n_pairs = pairs_per_active(w)
+
+    with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
+        ds = fc.upload(w.state(copy=False))
+        fc.set_timing(True)
+        with Clocks(local) as clk:
+            ms, st = time_steps(fc, ds, w, args.steps, args.warmup, fc.stream, torch, barrier)
+        clocks = clk.summary()
+        n_active = st["n_active"]
+        coal_ms = st["coal_ms"] / max(st["coal_launches"], 1)
+        # end to end through the host-pointer entry point (pinned buffers)
+        host = {k: v for k, v in w.state(copy=False).items() if v is not None}
+        np_dtype = np.float64 if precision == pkg.FSBM_FP64 else np.float32
+        pinned = {}
+        for k, v in host.items():
+            arr = np.ascontiguousarray(v, np_dtype if k == "spectra" else v.dtype)
+            t = torch.from_numpy(arr).pin_memory()
+            pinned[k] = t.numpy()
+        out_bytes = w.n_points * (8 + 8 + 4)
+        h2d = sum(a.nbytes for a in pinned.values())
+        d2h = pinned["spectra"].nbytes + out_bytes
+        fc.step_host(pinned, w.dt, w.n_steps)  # first call sizes the device mirrors
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fc.step_host(pinned, w.dt, w.n_steps)
+        e2e_s = time.perf_counter() - t0
+        barrier()
+
+    ms_max = ms
+    e2e_max = e2e_s
+    if dist:
+        tt = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_max, e2e_max = float(tt[0]), float(tt[1])
+    units = n_active * w.n_steps * args.steps * world
+    value = units / (ms_max / 1e3)
+
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    achieved = n_pairs * w.n_steps / (coal_ms / 1e3) / 1e9
+    peak = alu_peak_pairs(precision, sm_mhz) / 1e9
+    line = {
+        "metric": "grid-point coal updates/s at 33 & 264 bins; FP32 batched vs FP64 plain, same GPU",
+        "value": value,
+        "unit": "grid-point coal updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if precision == pkg.FSBM_FP64 else "f32+f64",
+        "data": "synthetic (seeded CONUS-12km-shaped blob cloud mask, log-normal spectra, gravitational-like kernels)",
+        "config": {
+            "workload": {"conus": "CONUS-12km-shaped 425x300x50 domain, 15% cloudy, 33 bins, 5 species, "
+                                  "dt=5 s x 10 collision steps per call",
+                         "stress": "264-bin 5-species stress points (20k), dt=2 s x 20 steps",
+                         "ragged": "ragged 33-264-bin 1-5-species batch (200k), dt=5 s x 10 steps"}[args.workload],
+            "form": "FP64 plain" if precision == pkg.FSBM_FP64 else "FP32 split",
+            "points": w.n_points,
+            "active_points": n_active,
+            "collision_steps_per_call": w.n_steps,
+            "bin_pairs_per_call": n_pairs * w.n_steps,
+            "l2": "inputs larger than L2 (spectra %.2f GB)" % (w.spectra.size * (8 if precision == 0 else 4) / 1e9),
+            "parallelism": f"dp{world} (independent points, weak scaling)",
+        },
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+        "e2e": {"value": units / e2e_max, "unit": "grid-point coal updates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 4 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_coal<%s>" % ("double" if precision == 0 else "float"),
+                     "peak_basis": "FP64 pipe %d/clk/SM / %d FP64 ops per pair" % (FP64_PER_CLK, FP64_OPS_PER_PAIR)
+                     if precision == 0 else "min(FP32 %d/clk/SM / %d ops, MUFU %d/clk/SM / %d ops) per pair" % (
+                         FP32_LANES, FP_OPS_PER_PAIR, MUFU_LANES, MUFU_OPS_PER_PAIR),
+                     "clock_mhz": sm_mhz, "coal_ms_per_launch": coal_ms},
+    }
+    if rank == 0 and not args.no_forms:
+        forms = {}
+        other = pkg.FSBM_FP32_SPLIT if precision == pkg.FSBM_FP64 else pkg.FSBM_FP64
+        r = run_form(pkg, torch, w, other, args.steps, 3, graph=(other == pkg.FSBM_FP32_SPLIT))
+        forms["conus_33bin_" + ("fp32_split_graph" if other else "fp64")] = r
+        forms["conus_33bin_" + ("fp64" if precision == 0 else "fp32_split")] = dict(
+            value=value, ms_per_step=ms_max / args.steps, coal_ms=coal_ms,
+            pairs_per_s=n_pairs * w.n_steps * args.steps / (ms_max / 1e3))
+        import synth
+        st32 = synth.config5(n_points=20_000, seed=5001)
+        r32 = run_form(pkg, torch, st32, pkg.FSBM_FP32_SPLIT, 2, 3, graph=True)
+        st64 = synth.subset(st32, np.arange(1000))
+        r64 = run_form(pkg, torch, st64, pkg.FSBM_FP64, 1, 3)
+        for key, rr, ww, pr in (("stress_264bin_fp32_split_graph", r32, st32, 1),
+                                ("stress_264bin_fp64", r64, st64, 0)):
+            rr["points"] = ww.n_points
+            kms = rr.get("coal_ms") or rr.get("step_ms_graph")
+            rr["alu_frac"] = (pairs_per_active(ww) * ww.n_steps / (kms / 1e3)) / alu_peak_pairs(pr, sm_mhz)
+            forms[key] = rr
+        fr = forms["conus_33bin_fp32_split_graph" if precision == 0 else "conus_33bin_fp64"]
+        kms = fr.get("coal_ms") or fr.get("step_ms_graph")
+        fr["alu_frac"] = (n_pairs * w.n_steps / (kms / 1e3)) / alu_peak_pairs(1 - precision, sm_mhz)
+        line["forms"] = forms
+        line["gpu_launches"] = 4 * args.steps
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_sample_run(w)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, world, rank):
+    """The CPU oracle as the reference arm: each step runs a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+
+    w = build_workload(args.workload, 0)
+    cores = oracle.max_threads()
+    act = np.nonzero((w.cloudy > 0) & (w.species_mask > 0))[0]
+    rng = np.random.default_rng(11)
+    # size the per-step sample to about 8 s of CPU work
+    n = min(len(act), 8 * cores)
+    while True:
+        ws = synth.subset(w, np.sort(rng.choice(act, n, replace=False)))
+        t0 = time.perf_counter()
+        oracle.run(ws)
+        el = time.perf_counter() - t0
+        if el > 2.0 or n >= len(act):
+            break
+        n = min(len(act), int(n * max(2.0, 8.0 / max(el, 1e-3))))
+    n = min(len(act), max(1, int(n * 8.0 / max(el, 1e-3))))
+    for _ in range(args.warmup):
+        ws = synth.subset(w, np.sort(rng.choice(act, max(1, n // 8), replace=False)))
+        oracle.run(ws)
+    total_t, total_u = 0.0, 0
+    for _ in range(args.steps):
+        ws = synth.subset(w, np.sort(rng.choice(act, n, replace=False)))
+        t0 = time.perf_counter()
+        oracle.run(ws)
+        total_t += time.perf_counter() - t0
+        total_u += n * w.n_steps
+    value = total_u / total_t
+    sample = f"{n} random active points of the domain x {w.n_steps} steps per bench step"
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "grid-point coal updates/s at 33 & 264 bins; FP32 batched vs FP64 plain, same GPU",
+        "value": value, "unit": "grid-point coal updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "CONUS-12km-shaped 425x300x50 domain, 15% cloudy, 33 bins, 5 species, "
+                               "dt=5 s x 10 collision steps per call", "form": "CPU oracle (FP64)",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "grid-point coal updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "grid-point coal updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * fsbm_coal.h -- C ABI of the GB300 (sm_103a) FSBM collision-coalescence library.
+ *
+ * The operation: one call advances, on the GPU, the bin spectra of a ragged batch of
+ * independent grid points by n_steps steps of the stochastic collection (collision-
+ * coalescence) update that WRF's Fast Spectral Bin Microphysics performs per grid point in
+ * coal_bott_new (arXiv 2409.07232, Sec. III, Listing 1). Collisions run only at points
+ * warmer than t_min_K (Listing 1: TT > 223.15 K), with pair collection kernels tabulated
+ * per species pair (Sec. V-A, Listing 2) and read per entry (Listing 4), over mass bins
+ * whose count the paper puts at 33, extendable to a few hundred (Sec. I); the cost is
+ * quadratic in the bin count (Sec. V-A). Grid points are independent (Sec. V-A).
+ *
+ * The arithmetic is Bott's flux method in the pairwise form: per step, with every pair of
+ * active bins reading start-of-step values,
+ *   N = M / x;  R^a_i = dt x_i N^a_i sum_{b,j} K_ab(i,j) N^b_j;  lambda = min(1, M / R);
+ *   C = K N^a_i N^b_j dt h min(lambda^a_i, lambda^b_j)   (h = 1/2 for a = b, i = j);
+ *   both partners lose C x; dM = C (x_i + x_j) goes to species P(a,b), bin
+ *   k = floor(log_alpha((x_i + x_j) / x_0)), and Bott's flux
+ *   F = dM e^{x1/2} (1 - e^{-c x1}) / x1, x1 = ln(M_{k+1} / (M_k + dM) + 1e-60),
+ *   c = (x_i + x_j - x_k) / (x_{k+1} - x_k), clipped to [0, dM], moves to bin k+1;
+ *   M' = M - loss + gain, round-off negatives set to 0, then M' scaled so that the
+ *   point's total mass equals its start-of-step total (FP64).
+ * Bins outside a species' active range [lo, hi] (first/last bin with M > 0 and
+ * M >= tau * max M) do not collect; a pair whose sum passes the top bin stays there.
+ *
+ * Units: CGS. M in g cm^-3, x in g, K in cm^3 s^-1, dt in s, T in K.
+ *
+ * Conventions for every entry point:
+ *  - Ownership: the context owns its device copies of the tables and its scratch memory;
+ *    the caller owns every state buffer. Spectra are updated in place; no output may alias
+ *    the spectra.
+ *  - Device pointers in fsbm_coal_state must be device memory of the context's device;
+ *    fsbm_coal_step_host takes host pointers instead.
+ *  - fsbm_coal_step is asynchronous on the context's stream. It allocates device memory
+ *    only when n_points exceeds every earlier call's; later calls allocate nothing and do
+ *    not synchronise the host.
+ *  - Errors: invalid arguments return FSBM_E_ARG before anything is launched; CUDA errors
+ *    return FSBM_E_CUDA; a message is kept for fsbm_coal_last_error. Bad data inside a
+ *    point (NaN, Inf, negative bins, an unknown grid id, a species mask or spectrum length
+ *    that does not match) never traps: the point is left unchanged and flagged in status.
+ *  - Thread safety: one context per host thread.
+ */
+#ifndef FSBM_COAL_H
+#define FSBM_COAL_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FSBM_API __attribute__((visibility("default")))
+#else
+#define FSBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsbm_coal_ctx fsbm_coal_ctx; /* opaque, library-owned */
+
+typedef enum {
+  FSBM_OK = 0,
+  FSBM_E_ARG = -1,         /* invalid argument; nothing launched                  */
+  FSBM_E_CUDA = -2,        /* a CUDA call failed; see fsbm_coal_last_error         */
+  FSBM_E_OOM = -3,         /* device allocation failed                            */
+  FSBM_E_TIMEOUT = -4,     /* reserved: a bounded device wait gave up             */
+  FSBM_E_UNSUPPORTED = -5  /* valid request this build does not implement         */
+} fsbm_status;
+
+typedef enum {
+  FSBM_FP64 = 0,        /* FP64 spectra and FP64 arithmetic throughout              */
+  FSBM_FP32_SPLIT = 1   /* FP32 spectra, FP32 pair fluxes and sums; FP64 budget,
+                           limiter ratios, update and renormalisation             */
+} fsbm_precision;
+
+/* Per-point status bits written by fsbm_coal_step. */
+enum {
+  FSBM_ST_LIMITED = 1,   /* the loss limiter fired (lambda < 1) in some bin and step   */
+  FSBM_ST_BADINPUT = 2,  /* NaN/Inf/negative bin, unknown grid, mask/length mismatch:
+                            point left unchanged                                       */
+  FSBM_ST_INACTIVE = 4   /* not cloudy, T <= t_min_K, or zero mass: left unchanged     */
+};
+
+typedef struct {
+  int32_t n_species;            /* species index space S, 1..5 (0 drops, 1 ice, 2 snow,
+                                   3 graupel, 4 hail by convention)                      */
+  int32_t n_grids;              /* 1..4 bin grids                                        */
+  const int32_t* bins_per_grid; /* host [n_grids], each 2..512 (33 s for s bins/doubling) */
+  const double* x0_g;           /* host [n_grids] smallest bin mass in g, > 0             */
+  const double* alpha;          /* host [n_grids] mass ratio of adjacent bins, 1 < a <= 2 */
+  const double* kernels;        /* host FP64 [grid][pair a<=b][n][n], finite, >= 0;
+                                   pair index a*S - a(a-1)/2 + (b-a); entry [i][j] is the
+                                   kernel of species a bin i with species b bin j; for a = b
+                                   only the upper triangle i <= j is read               */
+  const int8_t* product;        /* host [S][S] product species, P(a,b) = P(b,a) in {a,b};
+                                   NULL = max(a,b)                                         */
+  double t_min_K;               /* collisions only where T > t_min_K (223.15 in WRF)      */
+  double active_rel_threshold;  /* tau in [0, 1): active range cut-off relative to the
+                                   species' largest bin                                    */
+  int32_t precision;            /* fsbm_precision                                         */
+  int32_t mode;                 /* 0 = pairwise; other values: FSBM_E_UNSUPPORTED          */
+} fsbm_coal_config;
+
+typedef struct {                /* device pointers, caller-owned                          */
+  void* spectra;                /* double (FSBM_FP64) or float (FSBM_FP32_SPLIT), packed:
+                                   point p holds [stored species ascending][n_bins] at
+                                   element offset[p]; updated in place                     */
+  const int64_t* offset;        /* [n_points + 1] element offsets into spectra            */
+  const uint8_t* grid_id;       /* [n_points]                                             */
+  const uint8_t* species_mask;  /* [n_points] bit a set: species a stored                 */
+  const uint8_t* cloudy;        /* [n_points], 0 = skip; NULL = every point cloudy         */
+  const float* temperature;     /* [n_points] in K; NULL = every point warm enough         */
+  double* mass_budget;          /* [n_points] out: total mass B at the start of the call  */
+  double* mass_error;           /* [n_points] out: max over steps of |sum M' - B_s| / B_s
+                                   before renormalisation                                  */
+  int32_t* status;              /* [n_points] out: FSBM_ST_* bits                          */
+} fsbm_coal_state;
+
+/* Counters of the most recent step (read back with a stream synchronisation). */
+typedef struct {
+  int64_t n_points;             /* points passed                                          */
+  int64_t n_active;             /* points that passed the cloud/temperature/shape checks   */
+  int32_t block_dim;            /* threads per CTA of the collision kernel                */
+  int32_t grid_dim;             /* persistent CTAs                                        */
+  int32_t graph_replayed;       /* 1 if the last step was a CUDA-graph replay             */
+  int32_t reserved;
+  /* with timing on (fsbm_coal_set_timing), totals since the previous fsbm_coal_get_stats
+   * call, measured with CUDA events on the context's stream:                            */
+  double coal_ms;               /* collision-kernel time (steps launched without a graph) */
+  int64_t coal_launches;        /* collision-kernel launches timed                        */
+  double step_ms;               /* whole-step time (compaction + collision, any mode)     */
+  int64_t steps_timed;          /* steps timed                                            */
+} fsbm_coal_stats;
+
+/* Build a context: validates the configuration, derives every grid's pair tables (target
+ * bin offset and Courant number per bin distance), lays out the kernels for the device and
+ * copies them to the current CUDA device on `stream` (a cudaStream_t, NULL = default
+ * stream). Synchronises the stream before returning. *out receives the context. */
+FSBM_API fsbm_status fsbm_coal_init(const fsbm_coal_config* config, void* stream, fsbm_coal_ctx** out);
+
+/* Advance n_points points by n_steps steps of length dt (>= 0, finite) on the context's
+ * stream. Inputs and outputs are device pointers (see fsbm_coal_state). */
+FSBM_API fsbm_status fsbm_coal_step(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points,
+                           double dt, int32_t n_steps);
+
+/* Same as fsbm_coal_step with every fsbm_coal_state pointer in HOST memory: the arrays are
+ * copied to context-owned device buffers, stepped, and the spectra and outputs copied back.
+ * Synchronous (returns after the results are in host memory). Pinned host memory makes the
+ * copies faster. */
+FSBM_API fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* ctx, const fsbm_coal_state* host_state,
+                                int64_t n_points, double dt, int32_t n_steps);
+
+/* Time the collision kernel for each candidate CTA size on a copy of (a sample of) the
+ * given device state and keep the fastest for later steps. The caller's spectra are not
+ * modified. Synchronous. */
+FSBM_API fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points);
+
+/* Enable (1) or disable (0, the default) CUDA-graph capture of fsbm_coal_step: the first
+ * call with a given argument set records the launch sequence, later identical calls replay
+ * it. */
+FSBM_API fsbm_status fsbm_coal_set_graph(fsbm_coal_ctx* ctx, int32_t enable);
+
+/* Force the collision kernel's CTA size (0 = library default); for benchmarks and the
+ * autotuner's tests. Valid sizes: 128, 256, 512. */
+FSBM_API fsbm_status fsbm_coal_set_block(fsbm_coal_ctx* ctx, int32_t block_dim);
+
+/* Enable (1) or disable (0, the default) CUDA-event timing of the collision kernel and of
+ * whole steps; fsbm_coal_get_stats returns the totals. Costs two event records per step. */
+FSBM_API fsbm_status fsbm_coal_set_timing(fsbm_coal_ctx* ctx, int32_t enable);
+
+/* Synchronise the context's stream and fill *out with the last step's counters (and the
+ * timing totals, which it then resets). */
+FSBM_API fsbm_status fsbm_coal_get_stats(fsbm_coal_ctx* ctx, fsbm_coal_stats* out);
+
+/* Synchronise and copy the last step's compacted list of active point indices (in the
+ * order the collision kernel takes them: costliest class first, ascending point index
+ * within a class) to host memory `out` of capacity `cap` entries. *n_out receives the
+ * count (which may exceed cap; then only cap entries are written). */
+FSBM_API fsbm_status fsbm_coal_get_active_list(fsbm_coal_ctx* ctx, int32_t* out, int64_t cap, int64_t* n_out);
+
+/* Free the context and everything it owns. NULL is accepted. */
+FSBM_API fsbm_status fsbm_coal_destroy(fsbm_coal_ctx* ctx);
+
+/* Message of the context's last error ("" if none); a static message for NULL. */
+FSBM_API const char* fsbm_coal_last_error(const fsbm_coal_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSBM_COAL_H */

@@ -1,0 +1,604 @@
+// fsbm_coal.cu -- host side of the C ABI declared in include/fsbm_coal.h.
+//
+// fsbm_coal_init derives every grid's pair tables and lays the tabulated pair kernels out
+// for the device once, replacing the per-call kernel filling the paper profiled in
+// kernals_ks (Sec. V-A, Listing 2) with a lookup of one entry per bin pair (Listing 4).
+// fsbm_coal_step runs the compaction pass (the predicate array of Sec. V-B, Listing 5) and
+// the persistent collision kernel on the caller's stream, optionally as a CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fsbm_coal.h"
+#include "fsbm_internal.cuh"
+
+using namespace fsbm;
+
+struct fsbm_coal_ctx {
+  int S = 0, G = 0, precision = 0, device = 0, n_sms = 0;
+  cudaStream_t stream = nullptr;
+  Tables t{};
+  std::vector<void*> table_allocs;
+  // step scratch
+  Scratch scratch{};
+  int64_t cap_points = -1;
+  // host-pointer mirrors for fsbm_coal_step_host
+  void* h_spectra = nullptr;
+  size_t h_spectra_bytes = 0;
+  void* h_meta = nullptr;
+  size_t h_meta_bytes = 0;
+  // launch plan
+  int block_dim = 256;
+  CoalLaunch plan{};
+  bool plan_valid = false;
+  // CUDA graph of the last argument set
+  bool graph_enabled = false;
+  cudaGraphExec_t gexec = nullptr;
+  PointsDev g_points{};
+  int64_t g_n = -1;
+  double g_dt = 0.0;
+  int g_steps = -1;
+  CoalLaunch g_plan{};
+  bool last_replayed = false;
+  int64_t last_n = 0;
+  // CUDA-event timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_coal, ev_step;
+  std::string err;
+};
+
+namespace {
+
+const char* kNullCtxMsg = "fsbm_coal: null context";
+
+fsbm_status fail(fsbm_coal_ctx* c, fsbm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+fsbm_status cuda_fail(fsbm_coal_ctx* c, cudaError_t e, const char* what) {
+  const std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(c, e == cudaErrorMemoryAllocation ? FSBM_E_OOM : FSBM_E_CUDA, m);
+}
+
+#define CU(ctx, call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+int pair_index(int S, int a, int b) { return a * S - a * (a - 1) / 2 + (b - a); }
+
+// Kernel of species a bin i with species b bin j from the caller's [pair a<=b][n][n] block.
+double kern_entry(const double* Kg, int S, int n, int a, int i, int b, int j) {
+  const size_t nn = (size_t)n * n;
+  if (a < b) return Kg[(size_t)pair_index(S, a, b) * nn + (size_t)i * n + j];
+  if (a > b) return Kg[(size_t)pair_index(S, b, a) * nn + (size_t)j * n + i];
+  const int lo = std::min(i, j), hi = std::max(i, j);
+  return Kg[(size_t)pair_index(S, a, a) * nn + (size_t)lo * n + hi];
+}
+
+template <typename V>
+fsbm_status upload(fsbm_coal_ctx* c, const std::vector<V>& h, const V** out) {
+  void* d = nullptr;
+  CU(c, cudaMalloc(&d, sizeof(V) * std::max<size_t>(h.size(), 1)));
+  c->table_allocs.push_back(d);
+  if (!h.empty()) CU(c, cudaMemcpyAsync(d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, c->stream));
+  *out = static_cast<const V*>(d);
+  return FSBM_OK;
+}
+
+// Target-bin offset kappa(d) and Courant number c(d) of a bin pair at distance d on the grid
+// x_k = x0 alpha^k: x_i + x_j = x_max (1 + alpha^-d); its position above bin max(i,j) is
+// u = log_alpha(1 + alpha^-d). A position within 1e-9 of an integer is taken as exact
+// (c = 0): the i = j pair of the mass-doubling grid lands exactly one bin up.
+void pair_offsets(int n, double alpha, std::vector<int>& kap, std::vector<double>& cd) {
+  kap.assign(n, 0);
+  cd.assign(n, 0.0);
+  const double la = std::log(alpha);
+  for (int d = 0; d < n; ++d) {
+    const double r = std::pow(alpha, -(double)d);
+    const double u = std::log1p(r) / la;
+    const double m = std::floor(u + 0.5);
+    if (std::fabs(u - m) < 1e-9) {
+      kap[d] = (int)m;
+      cd[d] = 0.0;
+    } else {
+      const int k = (int)std::floor(u);
+      kap[d] = k;
+      cd[d] = k == 0 ? r / (alpha - 1.0) : ((1.0 + r) * std::pow(alpha, -(double)k) - 1.0) / (alpha - 1.0);
+    }
+  }
+}
+
+fsbm_status ensure_scratch(fsbm_coal_ctx* c, int64_t n_points) {
+  const int64_t nblk = (n_points + kCompactThreads - 1) / kCompactThreads;
+  if (n_points > c->cap_points) {
+    if (c->scratch.block_counts) cudaFree(c->scratch.block_counts);
+    if (c->scratch.active_list) cudaFree(c->scratch.active_list);
+    if (c->scratch.counters) cudaFree(c->scratch.counters);
+    c->scratch = Scratch{};
+    c->cap_points = -1;
+    CU(c, cudaMalloc(&c->scratch.block_counts, sizeof(int32_t) * std::max<int64_t>(1, nblk * kNumBuckets)));
+    CU(c, cudaMalloc(&c->scratch.active_list, sizeof(int32_t) * std::max<int64_t>(1, n_points)));
+    CU(c, cudaMalloc(&c->scratch.counters, sizeof(int32_t) * 4));
+    CU(c, cudaMemsetAsync(c->scratch.counters, 0, sizeof(int32_t) * 4, c->stream));
+    c->cap_points = n_points;
+  }
+  c->scratch.n_blocks = nblk;
+  return FSBM_OK;
+}
+
+fsbm_status ensure_plan(fsbm_coal_ctx* c) {
+  if (c->plan_valid) return FSBM_OK;
+  CU(c, coal_plan(c->t, c->precision, c->block_dim, c->n_sms, &c->plan));
+  c->plan_valid = true;
+  return FSBM_OK;
+}
+
+fsbm_status check_state(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt, int32_t n_steps) {
+  if (!s) return fail(c, FSBM_E_ARG, "fsbm_coal_step: state is NULL");
+  if (n_points < 0 || n_points > INT32_MAX - 1)
+    return fail(c, FSBM_E_ARG, "fsbm_coal_step: n_points must be in [0, 2^31 - 2]");
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(c, FSBM_E_ARG, "fsbm_coal_step: dt must be finite and >= 0");
+  if (n_steps < 0) return fail(c, FSBM_E_ARG, "fsbm_coal_step: n_steps must be >= 0");
+  if (n_points > 0 && (!s->spectra || !s->offset || !s->grid_id || !s->species_mask || !s->mass_budget ||
+                       !s->mass_error || !s->status))
+    return fail(c, FSBM_E_ARG, "fsbm_coal_step: a required state pointer is NULL");
+  return FSBM_OK;
+}
+
+PointsDev to_dev(const fsbm_coal_state* s) {
+  PointsDev p;
+  p.spectra = s->spectra;
+  p.offset = s->offset;
+  p.grid_id = s->grid_id;
+  p.species_mask = s->species_mask;
+  p.cloudy = s->cloudy;
+  p.temperature = s->temperature;
+  p.mass_budget = s->mass_budget;
+  p.mass_error = s->mass_error;
+  p.status = s->status;
+  return p;
+}
+
+bool same_points(const PointsDev& a, const PointsDev& b) { return std::memcmp(&a, &b, sizeof(PointsDev)) == 0; }
+
+fsbm_status take_events(fsbm_coal_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* out) {
+  cudaEvent_t e[2];
+  for (int q = 0; q < 2; ++q) {
+    if (!c->ev_pool.empty()) {
+      e[q] = c->ev_pool.back();
+      c->ev_pool.pop_back();
+    } else {
+      CU(c, cudaEventCreate(&e[q]));
+    }
+  }
+  *out = {e[0], e[1]};
+  return FSBM_OK;
+}
+
+fsbm_status enqueue(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps,
+                    const CoalLaunch& plan, bool capturing) {
+  CU(c, launch_compact(c->t, p, n_points, c->scratch, c->stream));
+  const bool timed = c->timing && !capturing;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{};
+  if (timed) {
+    fsbm_status st = take_events(c, &ev);
+    if (st != FSBM_OK) return st;
+    CU(c, cudaEventRecord(ev.first, c->stream));
+  }
+  CU(c, launch_coal(c->t, c->precision, p, c->scratch, dt, n_steps, plan, c->stream));
+  if (timed) {
+    CU(c, cudaEventRecord(ev.second, c->stream));
+    c->ev_coal.push_back(ev);
+  }
+  return FSBM_OK;
+}
+
+fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps);
+
+fsbm_status run_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps) {
+  fsbm_status st = ensure_scratch(c, n_points);
+  if (st != FSBM_OK) return st;
+  st = ensure_plan(c);
+  if (st != FSBM_OK) return st;
+  c->last_n = n_points;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{};
+  if (c->timing) {
+    st = take_events(c, &ev);
+    if (st != FSBM_OK) return st;
+    CU(c, cudaEventRecord(ev.first, c->stream));
+  }
+  st = launch_step(c, p, n_points, dt, n_steps);
+  if (st != FSBM_OK) return st;
+  if (c->timing) {
+    CU(c, cudaEventRecord(ev.second, c->stream));
+    c->ev_step.push_back(ev);
+  }
+  return FSBM_OK;
+}
+
+fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps) {
+  if (!c->graph_enabled) {
+    c->last_replayed = false;
+    return enqueue(c, p, n_points, dt, n_steps, c->plan, false);
+  }
+  const bool hit = c->gexec && same_points(p, c->g_points) && n_points == c->g_n && dt == c->g_dt &&
+                   n_steps == c->g_steps && std::memcmp(&c->plan, &c->g_plan, sizeof(CoalLaunch)) == 0;
+  if (!hit) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    fsbm_status est = enqueue(c, p, n_points, dt, n_steps, c->plan, true);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+    if (est != FSBM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return est;
+    }
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      c->gexec = nullptr;
+      return cuda_fail(c, ce, "cudaGraphInstantiate");
+    }
+    c->g_points = p;
+    c->g_n = n_points;
+    c->g_dt = dt;
+    c->g_steps = n_steps;
+    c->g_plan = c->plan;
+  }
+  CU(c, cudaGraphLaunch(c->gexec, c->stream));
+  c->last_replayed = hit;
+  return FSBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_ctx** out) {
+  if (!out) return FSBM_E_ARG;
+  *out = nullptr;
+  if (!cfg) return FSBM_E_ARG;
+  fsbm_coal_ctx* c = new fsbm_coal_ctx();
+  auto bail = [&](fsbm_status s) {
+    // keep the context only to report the message? no: the caller gets NULL; free everything
+    for (void* p : c->table_allocs) cudaFree(p);
+    delete c;
+    return s;
+  };
+  const int S = cfg->n_species, G = cfg->n_grids;
+  if (S < 1 || S > kMaxSpecies || G < 1 || G > kMaxGrids || !cfg->bins_per_grid || !cfg->x0_g || !cfg->alpha ||
+      !cfg->kernels)
+    return bail(FSBM_E_ARG);
+  if (cfg->precision != FSBM_FP64 && cfg->precision != FSBM_FP32_SPLIT) return bail(FSBM_E_ARG);
+  if (cfg->mode != 0) return bail(FSBM_E_UNSUPPORTED);
+  if (!std::isfinite(cfg->t_min_K) || !(cfg->active_rel_threshold >= 0.0) || !(cfg->active_rel_threshold < 1.0))
+    return bail(FSBM_E_ARG);
+  c->S = S;
+  c->G = G;
+  c->precision = cfg->precision;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->t.S = S;
+  c->t.G = G;
+  c->t.t_min = cfg->t_min_K;
+  c->t.tau = cfg->active_rel_threshold;
+  for (int a = 0; a < S; ++a)
+    for (int b = 0; b < S; ++b) {
+      const int p = cfg->product ? cfg->product[a * S + b] : std::max(a, b);
+      const int q = cfg->product ? cfg->product[b * S + a] : std::max(a, b);
+      if (p != q || (p != a && p != b)) return bail(FSBM_E_ARG);
+      c->t.product[a * S + b] = (int8_t)p;
+    }
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    return bail(FSBM_E_CUDA);
+
+  // LPT class ranks: costliest (grid, stored-species count) first
+  struct Cls { double cost; int g, ns; };
+  std::vector<Cls> cls;
+  size_t koff = 0;
+  const int npairs = S * (S + 1) / 2;
+  for (int g = 0; g < G; ++g) {
+    const int n = cfg->bins_per_grid[g];
+    const double x0 = cfg->x0_g[g], al = cfg->alpha[g];
+    if (n < 2 || n > kMaxBins || !(x0 > 0.0) || !std::isfinite(x0) || !(al > 1.0) || !(al <= 2.0))
+      return bail(FSBM_E_ARG);
+    const double* Kg = cfg->kernels + koff;
+    const size_t nn = (size_t)n * n;
+    for (size_t e = 0; e < (size_t)npairs * nn; ++e)
+      if (!(Kg[e] >= 0.0) || !std::isfinite(Kg[e])) return bail(FSBM_E_ARG);
+    koff += (size_t)npairs * nn;
+    for (int ns = 1; ns <= S; ++ns)
+      cls.push_back(Cls{(double)ns * n * (n + 1) / 2.0 + (double)ns * (ns - 1) / 2.0 * (double)n * n, g, ns});
+
+    GridDev& gd = c->t.g[g];
+    gd.n = n;
+    std::vector<int> kap;
+    std::vector<double> cd;
+    pair_offsets(n, al, kap, cd);
+    gd.kappa_max = kap[0];
+    if (gd.kappa_max > kMaxKappa) return bail(FSBM_E_ARG);
+    for (int q = 0; q <= kMaxKappa; ++q) {
+      gd.d_lo[q] = n;
+      gd.d_hi[q] = -1;
+    }
+    for (int d = 0; d < n; ++d) {
+      if (d > 0 && kap[d] > kap[d - 1]) return bail(FSBM_E_ARG);  // not monotone: not a geometric grid
+      gd.d_lo[kap[d]] = std::min(gd.d_lo[kap[d]], d);
+      gd.d_hi[kap[d]] = std::max(gd.d_hi[kap[d]], d);
+    }
+    std::vector<double> x(n), Kd((size_t)S * S * nn, 0.0), Kr((size_t)S * S * nn, 0.0);
+    for (int k = 0; k < n; ++k) x[k] = x0 * std::pow(al, (double)k);
+    for (int s = 0; s < S; ++s)
+      for (int l = 0; l < S; ++l) {
+        double* kd = Kd.data() + (size_t)(s * S + l) * nn;
+        double* kr = Kr.data() + (size_t)(s * S + l) * nn;
+        for (int d = 0; d < n; ++d)
+          for (int m = d; m < n; ++m) kd[(size_t)d * n + m] = kern_entry(Kg, S, n, s, m - d, l, m);
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) kr[(size_t)j * n + i] = kern_entry(Kg, S, n, s, i, l, j);
+      }
+    std::vector<float> x32(x.begin(), x.end()), cd32(cd.begin(), cd.end()), Kd32(Kd.begin(), Kd.end()),
+        Kr32(Kr.begin(), Kr.end());
+    fsbm_status st;
+    if ((st = upload(c, x, &gd.x64)) != FSBM_OK || (st = upload(c, x32, &gd.x32)) != FSBM_OK ||
+        (st = upload(c, cd, &gd.cd64)) != FSBM_OK || (st = upload(c, cd32, &gd.cd32)) != FSBM_OK ||
+        (st = upload(c, Kd, &gd.Kd64)) != FSBM_OK || (st = upload(c, Kd32, &gd.Kd32)) != FSBM_OK ||
+        (st = upload(c, Kr, &gd.Kr64)) != FSBM_OK || (st = upload(c, Kr32, &gd.Kr32)) != FSBM_OK)
+      return bail(st);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(FSBM_E_CUDA);
+  }
+  std::stable_sort(cls.begin(), cls.end(), [](const Cls& a, const Cls& b) { return a.cost > b.cost; });
+  std::memset(c->t.bucket_rank, -1, sizeof(c->t.bucket_rank));
+  for (size_t r = 0; r < cls.size(); ++r) c->t.bucket_rank[cls[r].g * (kMaxSpecies + 1) + cls[r].ns] = (int8_t)r;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(FSBM_E_CUDA);
+  *out = c;
+  return FSBM_OK;
+}
+
+fsbm_status fsbm_coal_step(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt,
+                           int32_t n_steps) {
+  if (!c) return FSBM_E_ARG;
+  fsbm_status st = check_state(c, s, n_points, dt, n_steps);
+  if (st != FSBM_OK) return st;
+  return run_step(c, to_dev(s), n_points, dt, n_steps);
+}
+
+fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int64_t n_points, double dt,
+                                int32_t n_steps) {
+  if (!c) return FSBM_E_ARG;
+  fsbm_status st = check_state(c, h, n_points, dt, n_steps);
+  if (st != FSBM_OK) return st;
+  if (n_points == 0) return FSBM_OK;
+  const size_t esz = c->precision == FSBM_FP64 ? sizeof(double) : sizeof(float);
+  const int64_t base = h->offset[0], total = h->offset[n_points] - base;
+  if (base < 0 || total < 0) return fail(c, FSBM_E_ARG, "fsbm_coal_step_host: offsets must be non-decreasing");
+  const size_t spec_bytes = (size_t)total * esz;
+  // device mirror of the metadata and outputs: offsets, outputs, then byte arrays
+  const size_t n = (size_t)n_points;
+  const size_t meta = sizeof(int64_t) * (n + 1) + sizeof(double) * 2 * n + sizeof(int32_t) * n + sizeof(float) * n +
+                      3 * n + 64;
+  if (spec_bytes > c->h_spectra_bytes) {
+    if (c->h_spectra) cudaFree(c->h_spectra);
+    c->h_spectra = nullptr;
+    c->h_spectra_bytes = 0;
+    CU(c, cudaMalloc(&c->h_spectra, std::max<size_t>(spec_bytes, 16)));
+    c->h_spectra_bytes = spec_bytes;
+  }
+  if (meta > c->h_meta_bytes) {
+    if (c->h_meta) cudaFree(c->h_meta);
+    c->h_meta = nullptr;
+    c->h_meta_bytes = 0;
+    CU(c, cudaMalloc(&c->h_meta, meta));
+    c->h_meta_bytes = meta;
+  }
+  char* m = static_cast<char*>(c->h_meta);
+  int64_t* d_off = reinterpret_cast<int64_t*>(m);
+  m += sizeof(int64_t) * (n + 1);
+  double* d_bud = reinterpret_cast<double*>(m);
+  m += sizeof(double) * n;
+  double* d_err = reinterpret_cast<double*>(m);
+  m += sizeof(double) * n;
+  int32_t* d_st = reinterpret_cast<int32_t*>(m);
+  m += sizeof(int32_t) * n;
+  float* d_T = reinterpret_cast<float*>(m);
+  m += sizeof(float) * n;
+  uint8_t* d_gid = reinterpret_cast<uint8_t*>(m);
+  uint8_t* d_mask = d_gid + n;
+  uint8_t* d_cl = d_mask + n;
+  char* d_spec = static_cast<char*>(c->h_spectra);
+  cudaStream_t sm = c->stream;
+  CU(c, cudaMemcpyAsync(d_spec, static_cast<const char*>(h->spectra) + (size_t)base * esz, spec_bytes,
+                        cudaMemcpyHostToDevice, sm));
+  CU(c, cudaMemcpyAsync(d_off, h->offset, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, sm));
+  CU(c, cudaMemcpyAsync(d_gid, h->grid_id, n, cudaMemcpyHostToDevice, sm));
+  CU(c, cudaMemcpyAsync(d_mask, h->species_mask, n, cudaMemcpyHostToDevice, sm));
+  if (h->cloudy) CU(c, cudaMemcpyAsync(d_cl, h->cloudy, n, cudaMemcpyHostToDevice, sm));
+  if (h->temperature) CU(c, cudaMemcpyAsync(d_T, h->temperature, sizeof(float) * n, cudaMemcpyHostToDevice, sm));
+  PointsDev p;
+  p.spectra = d_spec - (size_t)base * esz;  // the offsets index from the caller's base
+  p.offset = d_off;
+  p.grid_id = d_gid;
+  p.species_mask = d_mask;
+  p.cloudy = h->cloudy ? d_cl : nullptr;
+  p.temperature = h->temperature ? d_T : nullptr;
+  p.mass_budget = d_bud;
+  p.mass_error = d_err;
+  p.status = d_st;
+  st = run_step(c, p, n_points, dt, n_steps);
+  if (st != FSBM_OK) return st;
+  CU(c, cudaMemcpyAsync(static_cast<char*>(h->spectra) + (size_t)base * esz, d_spec, spec_bytes,
+                        cudaMemcpyDeviceToHost, sm));
+  CU(c, cudaMemcpyAsync(h->mass_budget, d_bud, sizeof(double) * n, cudaMemcpyDeviceToHost, sm));
+  CU(c, cudaMemcpyAsync(h->mass_error, d_err, sizeof(double) * n, cudaMemcpyDeviceToHost, sm));
+  CU(c, cudaMemcpyAsync(h->status, d_st, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, sm));
+  CU(c, cudaStreamSynchronize(sm));
+  return FSBM_OK;
+}
+
+fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points) {
+  if (!c) return FSBM_E_ARG;
+  fsbm_status st = check_state(c, s, n_points, 1.0, 1);
+  if (st != FSBM_OK) return st;
+  if (n_points == 0) return FSBM_OK;
+  const int64_t P = std::min<int64_t>(n_points, 1 << 17);
+  int64_t off[2];
+  CU(c, cudaMemcpyAsync(&off[0], s->offset, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaMemcpyAsync(&off[1], s->offset + P, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaStreamSynchronize(c->stream));
+  const size_t esz = c->precision == FSBM_FP64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = (size_t)(off[1] - off[0]) * esz;
+  char* tmp = nullptr;
+  const size_t outb = (sizeof(double) * 2 + sizeof(int32_t)) * (size_t)P;
+  CU(c, cudaMalloc(&tmp, bytes + outb + 64));
+  char* src = static_cast<char*>(s->spectra) + (size_t)off[0] * esz;
+  PointsDev p = to_dev(s);
+  p.spectra = tmp - (size_t)off[0] * esz;
+  p.mass_budget = reinterpret_cast<double*>(tmp + ((bytes + 15) & ~size_t(15)));
+  p.mass_error = p.mass_budget + P;
+  p.status = reinterpret_cast<int32_t*>(p.mass_error + P);
+  st = ensure_scratch(c, std::max<int64_t>(n_points, P));
+  if (st != FSBM_OK) {
+    cudaFree(tmp);
+    return st;
+  }
+  c->scratch.n_blocks = (P + kCompactThreads - 1) / kCompactThreads;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cands[3] = {128, 256, 512};
+  float best = 1e30f;
+  int best_b = c->block_dim;
+  for (int b : cands) {
+    CoalLaunch plan;
+    if (coal_plan(c->t, c->precision, b, c->n_sms, &plan) != cudaSuccess) continue;
+    float ms_tot = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+      launch_compact(c->t, p, P, c->scratch, c->stream);
+      cudaEventRecord(e0, c->stream);
+      launch_coal(c->t, c->precision, p, c->scratch, 5.0, 1, plan, c->stream);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep) ms_tot += ms;
+    }
+    if (ms_tot < best) {
+      best = ms_tot;
+      best_b = b;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const cudaError_t le = cudaGetLastError();
+  cudaFree(tmp);
+  if (le != cudaSuccess) return cuda_fail(c, le, "fsbm_coal_autotune");
+  c->block_dim = best_b;
+  c->plan_valid = false;
+  return ensure_plan(c);
+}
+
+fsbm_status fsbm_coal_set_graph(fsbm_coal_ctx* c, int32_t enable) {
+  if (!c) return FSBM_E_ARG;
+  c->graph_enabled = enable != 0;
+  if (!c->graph_enabled && c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return FSBM_OK;
+}
+
+fsbm_status fsbm_coal_set_block(fsbm_coal_ctx* c, int32_t block_dim) {
+  if (!c) return FSBM_E_ARG;
+  if (block_dim == 0) block_dim = 256;
+  if (block_dim != 128 && block_dim != 256 && block_dim != 512)
+    return fail(c, FSBM_E_ARG, "fsbm_coal_set_block: block_dim must be 128, 256 or 512");
+  c->block_dim = block_dim;
+  c->plan_valid = false;
+  return ensure_plan(c);
+}
+
+fsbm_status fsbm_coal_set_timing(fsbm_coal_ctx* c, int32_t enable) {
+  if (!c) return FSBM_E_ARG;
+  c->timing = enable != 0;
+  return FSBM_OK;
+}
+
+fsbm_status fsbm_coal_get_stats(fsbm_coal_ctx* c, fsbm_coal_stats* out) {
+  if (!c || !out) return FSBM_E_ARG;
+  std::memset(out, 0, sizeof(*out));
+  CU(c, cudaStreamSynchronize(c->stream));
+  for (auto* lst : {&c->ev_coal, &c->ev_step}) {
+    double tot = 0.0;
+    for (auto& ev : *lst) {
+      float ms = 0.f;
+      CU(c, cudaEventElapsedTime(&ms, ev.first, ev.second));
+      tot += ms;
+      c->ev_pool.push_back(ev.first);
+      c->ev_pool.push_back(ev.second);
+    }
+    if (lst == &c->ev_coal) {
+      out->coal_ms = tot;
+      out->coal_launches = (int64_t)lst->size();
+    } else {
+      out->step_ms = tot;
+      out->steps_timed = (int64_t)lst->size();
+    }
+    lst->clear();
+  }
+  int32_t cnt[2] = {0, 0};
+  if (c->scratch.counters) CU(c, cudaMemcpy(cnt, c->scratch.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+  out->n_points = c->last_n;
+  out->n_active = cnt[0];
+  out->block_dim = c->plan.block_dim;
+  out->grid_dim = c->plan.grid_dim;
+  out->graph_replayed = c->last_replayed ? 1 : 0;
+  return FSBM_OK;
+}
+
+fsbm_status fsbm_coal_get_active_list(fsbm_coal_ctx* c, int32_t* out, int64_t cap, int64_t* n_out) {
+  if (!c || !n_out || cap < 0 || (cap > 0 && !out)) return FSBM_E_ARG;
+  *n_out = 0;
+  CU(c, cudaStreamSynchronize(c->stream));
+  if (!c->scratch.counters) return FSBM_OK;
+  int32_t cnt = 0;
+  CU(c, cudaMemcpy(&cnt, c->scratch.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+  *n_out = cnt;
+  const int64_t m = std::min<int64_t>(cap, cnt);
+  if (m > 0) CU(c, cudaMemcpy(out, c->scratch.active_list, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
+  return FSBM_OK;
+}
+
+fsbm_status fsbm_coal_destroy(fsbm_coal_ctx* c) {
+  if (!c) return FSBM_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (void* p : c->table_allocs) cudaFree(p);
+  if (c->scratch.block_counts) cudaFree(c->scratch.block_counts);
+  if (c->scratch.active_list) cudaFree(c->scratch.active_list);
+  if (c->scratch.counters) cudaFree(c->scratch.counters);
+  if (c->h_spectra) cudaFree(c->h_spectra);
+  if (c->h_meta) cudaFree(c->h_meta);
+  for (auto& ev : c->ev_coal) c->ev_pool.insert(c->ev_pool.end(), {ev.first, ev.second});
+  for (auto& ev : c->ev_step) c->ev_pool.insert(c->ev_pool.end(), {ev.first, ev.second});
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return FSBM_OK;
+}
+
+const char* fsbm_coal_last_error(const fsbm_coal_ctx* c) { return c ? c->err.c_str() : kNullCtxMsg; }
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// fsbm_internal.cuh -- device-side data shared by the library's translation units.
+//
+// Layout of everything the kernels read, per grid (all device memory, context-owned):
+//   kappa[d], cd[d]   target-bin offset and Courant number of a bin pair at distance
+//                     d = |i - j|: on a geometric grid x_k = x0 alpha^k the pair's mass
+//                     x_i + x_j = x_max (1 + alpha^-d) lands in bin max(i,j) + kappa[d]
+//                     with c = ((1 + alpha^-d) alpha^-kappa - 1) / (alpha - 1), so both
+//                     depend on d only (the pair tables of Sec. V-A shrink to length n).
+//   x[k]              bin masses.
+//   Kd[s][l][d][m]    kernel of species s bin m-d with species l bin m (m fastest): the
+//                     layout the gain pass walks, one lane per target bin, d in lock-step.
+//   Kr[a][b][j][i]    kernel of species a bin i with species b bin j (i fastest): the
+//                     layout of the loss mat-vec, one lane per row i.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fsbm {
+
+constexpr int kMaxSpecies = 5;
+constexpr int kMaxGrids = 4;
+constexpr int kMaxBins = 512;
+constexpr int kMaxKappa = 15;      // kappa[0] = floor(log_alpha 2) <= 15 -> alpha >= 2^(1/15)
+constexpr int kMaxOrient = kMaxSpecies * kMaxSpecies;
+constexpr int kNumBuckets = kMaxGrids * kMaxSpecies;
+
+// Bott's constant added to the bin ratio before its logarithm (FP64 form).
+constexpr double kBottEps = 1e-60;
+// ln(1e-60): the FP32 form clamps the logarithm here instead of adding 1e-60.
+constexpr float kLnBottEps = -138.15510557964274f;
+
+struct GridDev {
+  int n;
+  int kappa_max;                  // kappa[0]
+  int d_lo[kMaxKappa + 1];        // D_kappa = {d : kappa[d] = kappa} = [d_lo, d_hi]
+  int d_hi[kMaxKappa + 1];
+  const double* x64;
+  const float* x32;
+  const double* cd64;
+  const float* cd32;
+  const double* Kd64;
+  const float* Kd32;
+  const double* Kr64;
+  const float* Kr32;
+};
+
+struct Tables {
+  int S;
+  int G;
+  double t_min;
+  double tau;
+  int8_t product[kMaxSpecies * kMaxSpecies];
+  int8_t bucket_rank[kMaxGrids * (kMaxSpecies + 1)];  // [g][n stored species] -> LPT rank
+  GridDev g[kMaxGrids];
+};
+
+// Caller-owned per-point arrays (device pointers).
+struct PointsDev {
+  void* spectra;
+  const int64_t* offset;
+  const uint8_t* grid_id;
+  const uint8_t* species_mask;
+  const uint8_t* cloudy;
+  const float* temperature;
+  double* mass_budget;
+  double* mass_error;
+  int32_t* status;
+};
+
+// Context-owned scratch of one step.
+struct Scratch {
+  int32_t* block_counts;   // [kNumBuckets][n_blocks]
+  int32_t* active_list;    // [n_points]
+  int32_t* counters;       // [0] active count, [1] queue head
+  int64_t n_blocks;
+};
+
+constexpr int kCompactThreads = 256;
+
+// compact.cu
+cudaError_t launch_compact(const Tables& t, const PointsDev& p, int64_t n_points, const Scratch& s,
+                           cudaStream_t stream);
+
+// coal_kernel.cu
+struct CoalLaunch {
+  int block_dim;
+  int grid_dim;
+  size_t smem;
+};
+cudaError_t coal_plan(const Tables& t, int precision, int block_dim, int n_sms, CoalLaunch* out);
+cudaError_t launch_coal(const Tables& t, int precision, const PointsDev& p, const Scratch& s, double dt,
+                        int n_steps, const CoalLaunch& plan, cudaStream_t stream);
+
+}  // namespace fsbm

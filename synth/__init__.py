@@ -19,6 +19,7 @@ from .workloads import (  # noqa: F401
     config3,
     config4,
     config5,
+    conus_sample,
     custom_points,
     subset,
 )

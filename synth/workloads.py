@@ -258,7 +258,8 @@ def _lognormal_points(rng, grid_id, mask, grids, S, offset, spectra):
     e = rng.exponential(size=(P, S))
     present = ((mask[:, None].astype(np.int64) >> np.arange(S)[None, :]) & 1).astype(bool)
     e = np.where(present, e, 0.0)
-    share = e / e.sum(axis=1, keepdims=True)
+    tot = e.sum(axis=1, keepdims=True)
+    share = np.divide(e, tot, out=np.zeros_like(e), where=tot > 0)
     # slot of species a at point p = number of stored species below a
     slot = np.cumsum(present, axis=1) - 1
     for g, (n, x0, alpha) in enumerate(grids):
@@ -280,18 +281,22 @@ def _lognormal_points(rng, grid_id, mask, grids, S, offset, spectra):
     del ns
 
 
-def config2(shape=(425, 300, 50), seed: int = 2001, frac=0.15, n_points: Optional[int] = None) -> Workload:
+def config2(shape=(425, 300, 50), seed: int = 2001, frac=0.15, n_points: Optional[int] = None,
+            points: Optional[np.ndarray] = None) -> Workload:
     """CONUS-12km-shaped domain: 425 x 300 x 50 points, 15 % cloudy by a blob mask,
     33 bins, 5 species, gravitational-like tables, dt = 5 s, 10 steps, T = 263 K.
 
     Non-cloudy points store no species (empty spectra). ``n_points`` keeps only the first
-    points of the flattened domain (a smaller, same-shaped sample)."""
+    points of the flattened domain; ``points`` keeps the given flat indices (a sample of the
+    whole domain; its spectra are drawn for the kept points only)."""
     rng = np.random.default_rng(seed)
     S = 5
     n, x0, alpha = mass_grid(1)
     cloudy = conus_cloud_mask(shape, frac=frac, rng=rng)
     if n_points is not None:
         cloudy = cloudy[:n_points]
+    if points is not None:
+        cloudy = cloudy[np.asarray(points, np.int64)]
     P = cloudy.size
     mask = np.where(cloudy > 0, (1 << S) - 1, 0).astype(np.uint8)
     grid_id = np.zeros(P, np.uint8)
@@ -304,6 +309,15 @@ def config2(shape=(425, 300, 50), seed: int = 2001, frac=0.15, n_points: Optiona
         kernels=kern, product=default_product(S), spectra=spectra, offset=offset, grid_id=grid_id,
         species_mask=mask, cloudy=cloudy, temperature=np.full(P, 263.0, np.float32),
         dt=5.0, n_steps=10, tau=0.0, meta=dict(shape=shape))
+
+
+def conus_sample(n_cloudy: int, n_clear: int, seed: int = 7, shape=(425, 300, 50)) -> Workload:
+    """A seeded sample of config 2's domain: n_cloudy cloudy and n_clear clear points."""
+    mask = conus_cloud_mask(shape, rng=np.random.default_rng(2001))
+    rng = np.random.default_rng(seed)
+    cl = rng.choice(np.nonzero(mask)[0], n_cloudy, replace=False)
+    cr = rng.choice(np.nonzero(mask == 0)[0], n_clear, replace=False)
+    return config2(shape=shape, points=np.sort(np.concatenate([cl, cr])))
 
 
 def config3(n_points: int = 1024, seed: int = 1001) -> Workload:
