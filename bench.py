@@ -158,16 +158,40 @@ def cpu_sample_run(w, budget_s=12.0, seed=3):
                        f"({elapsed:.1f} s, FP64 C oracle, OpenMP over points)")
 
 
-def build_workload(name, rank):
+def build_workload(name, rank, points=None):
     import synth
 
+    off = rank_seed_offset(rank)
     if name == "conus":
-        return synth.config2(seed=2001 + 1000 * rank)
+        if points:
+            return synth.conus_sample(points, points // 4, seed=7 + off)
+        return synth.config2(seed=2001 + off)
     if name == "stress":
-        return synth.config5(n_points=20_000, seed=5001 + 1000 * rank)
+        return synth.config5(n_points=20_000, seed=5001 + off)
     if name == "ragged":
-        return synth.config4(n_points=200_000, seed=4001 + 1000 * rank)
+        return synth.config4(n_points=200_000, seed=4001 + off)
     raise ValueError(name)
+
+
+def rank_seed_offset(rank):
+    """Seed offset of a rank's own domain: ranks run independent domains (weak scaling)."""
+    return 1000 * rank
+
+
+def aggregate_times(values, dist=None, device="cpu"):
+    """Max over ranks of each timing (the slowest rank bounds the step); no data is exchanged."""
+    if dist is None:
+        return list(values)
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units all ranks processed divided by the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
 
 
 def time_steps(fc, ds, w, steps, warmup, stream, torch, barrier=None):
@@ -227,6 +251,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32 and 264-bin side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--points", type=int, default=0,
+                    help="CONUS workload: a seeded sample of this many cloudy points (plus a quarter as many "
+                         "clear ones) instead of the whole domain; for profiling runs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -252,7 +279,7 @@ def main():
             dist.barrier()
 
     precision = pkg.FSBM_FP64 if args.precision == "fp64" else pkg.FSBM_FP32_SPLIT
-    w = build_workload(args.workload, rank)
+    w = build_workload(args.workload, rank, args.points)
     n_pairs = pairs_per_active(w)
 
     with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
@@ -282,14 +309,9 @@ def main():
         e2e_s = time.perf_counter() - t0
         barrier()
 
-    ms_max = ms
-    e2e_max = e2e_s
-    if dist:
-        tt = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_max, e2e_max = float(tt[0]), float(tt[1])
+    ms_max, e2e_max = aggregate_times([ms, e2e_s], dist, device="cuda")
+    value = whole_job_rate(n_active * w.n_steps * args.steps, world, ms_max)
     units = n_active * w.n_steps * args.steps * world
-    value = units / (ms_max / 1e3)
 
     sm_mhz = clocks["sm_mhz"] or 2070.0
     achieved = n_pairs * w.n_steps / (coal_ms / 1e3) / 1e9

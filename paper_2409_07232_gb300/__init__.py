@@ -25,6 +25,7 @@ from .binding import (  # noqa: F401
     fsbm_coal_get_stats,
     fsbm_coal_init,
     fsbm_coal_last_error,
+    fsbm_coal_math_check,
     fsbm_coal_set_block,
     fsbm_coal_set_graph,
     fsbm_coal_set_timing,

@@ -37,7 +37,7 @@ _STATUS_NAMES = {0: "FSBM_OK", -1: "FSBM_E_ARG", -2: "FSBM_E_CUDA", -3: "FSBM_E_
 # Every entry point include/fsbm_coal.h declares.
 EXPORTS = ("fsbm_coal_init", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_autotune",
            "fsbm_coal_set_graph", "fsbm_coal_set_block", "fsbm_coal_set_timing", "fsbm_coal_get_stats",
-           "fsbm_coal_get_active_list", "fsbm_coal_destroy", "fsbm_coal_last_error")
+           "fsbm_coal_get_active_list", "fsbm_coal_math_check", "fsbm_coal_destroy", "fsbm_coal_last_error")
 
 
 class FsbmError(RuntimeError):
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
             "fsbm_coal_set_timing": ([V, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_get_stats": ([V, P(fsbm_coal_stats)], ctypes.c_int),
             "fsbm_coal_get_active_list": ([V, V, ctypes.c_int64, P(ctypes.c_int64)], ctypes.c_int),
+            "fsbm_coal_math_check": ([V, V], ctypes.c_int),
             "fsbm_coal_destroy": ([V], ctypes.c_int),
             "fsbm_coal_last_error": ([V], ctypes.c_char_p),
         }
@@ -212,6 +213,12 @@ def fsbm_coal_get_active_list(ctx, cap: int) -> np.ndarray:
     _check(ctx, load().fsbm_coal_get_active_list(ctx, out.ctypes.data, int(cap), ctypes.byref(n)),
            "fsbm_coal_get_active_list")
     return out[:min(int(cap), n.value)].copy()
+
+
+def fsbm_coal_math_check(ctx) -> np.ndarray:
+    out = np.zeros(3, np.float64)
+    _check(ctx, load().fsbm_coal_math_check(ctx, out.ctypes.data), "fsbm_coal_math_check")
+    return out
 
 
 def fsbm_coal_destroy(ctx) -> None:

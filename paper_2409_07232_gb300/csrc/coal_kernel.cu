@@ -36,7 +36,7 @@ struct Orient {
                     // other orientation of the same species pair)
   int8_t half;      // same species: the diagonal pair counts once, h = 1/2
   int8_t c;         // slot of the product species
-  int table;        // element offset of Kd[s][l] in the grid's table
+  int table;        // s_id * S + l_id: position of the orientation inside a Kd row
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -108,6 +108,50 @@ __device__ __forceinline__ float bott_flux(float dM, float Mk, float Mk1, float 
   return fminf(fmaxf(F, 0.f), dM);
 }
 
+// FP32 flux, fast form. rho from the SFU reciprocal (2 ulp); ln rho = (e + log2 m) ln 2 with
+// m in [1/sqrt2, sqrt2), where the SFU's log2 has an absolute error near 2^-22.6, so ln rho
+// keeps an absolute error near 1e-7 at any magnitude; e^{x1/2} = sqrt(rho) through the SFU
+// reciprocal square root. (1 - e^{-z}) / x1 with z = c x1 is c times the series of
+// (1 - e^{-z}) / z for |z| <= 1/2 (nine terms, relative error below 1e-8), and the direct
+// form otherwise. rho = 0 (empty bin k+1) takes ln rho = ln 1e-60, e^{x1/2} = 1e-30 exactly
+// as the clamped FP32 reading does; subnormal or overflowing ratios use bott_flux above.
+__device__ __forceinline__ float bott_flux_f32(float dM, float Mk, float Mk1, float c) {
+  const float g = Mk + dM;
+  const float rho = __fdividef(Mk1, g);
+  float x1, A;
+  if (rho >= 1.17549435e-38f && rho <= 3.0e38f) {
+    const int ix = __float_as_int(rho);
+    const int e = (ix - 0x3f3504f3) >> 23;
+    const float m = __int_as_float(ix - (e << 23));
+    x1 = fmaf((float)e, 0.693147182f, __log2f(m) * 0.693147182f);
+    x1 = fminf(fmaxf(x1, kLnBottEps), 80.f);
+    A = rho * rsqrtf(rho);
+  } else if (rho == 0.f) {
+    x1 = kLnBottEps;
+    A = 1.0e-30f;
+  } else {
+    return bott_flux(dM, Mk, Mk1, c);
+  }
+  const float z = c * x1;
+  float ratio;
+  if (fabsf(z) <= 0.5f) {
+    // (1 - e^{-z}) / z = sum_k (-z)^k / (k+1)!, k = 0..8
+    float q = fmaf(z, 1.f / 3628800.f, -1.f / 362880.f);
+    q = fmaf(q, z, 1.f / 40320.f);
+    q = fmaf(q, z, -1.f / 5040.f);
+    q = fmaf(q, z, 1.f / 720.f);
+    q = fmaf(q, z, -1.f / 120.f);
+    q = fmaf(q, z, 1.f / 24.f);
+    q = fmaf(q, z, -1.f / 6.f);
+    q = fmaf(q, z, 0.5f);
+    q = fmaf(q, -z, 1.f);
+    ratio = c * q;
+  } else {
+    ratio = __fdividef(1.f - expf(-z), x1);
+  }
+  return fminf(dM * A * ratio, dM);
+}
+
 template <typename T> struct Sel;
 template <> struct Sel<double> {
   static __device__ const double* x(const GridDev& g) { return g.x64; }
@@ -122,23 +166,85 @@ template <> struct Sel<float> {
   static __device__ const float* Kr(const GridDev& g) { return g.Kr32; }
 };
 
+// Running sums. The FP64 form adds each term in FP64. The FP32 form adds short runs of
+// terms in FP32 and folds each run into a float-float total (hi + lo, Knuth's two-sum), so
+// rounding grows with the run length (16 or 32 terms) rather than with a sum over a few
+// hundred bins, and no FP64 instruction enters the pair loops.
+struct FF {
+  float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void ff_add(FF& a, float v) {
+  const float s = a.hi + v;
+  const float bp = s - a.hi;
+  const float e = (a.hi - (s - bp)) + (v - bp);
+  a.hi = s;
+  a.lo += e;
+}
+__device__ __forceinline__ void ff_add(FF& a, const FF& b) {
+  ff_add(a, b.hi);
+  a.lo += b.lo;
+}
+
+template <typename T> struct Num;
+template <> struct Num<double> {
+  using Sum = double;
+  static __device__ __forceinline__ void add(Sum& a, const Sum& b) { a += b; }
+  static __device__ __forceinline__ void sub(Sum& a, const Sum& b) { a -= b; }
+  static __device__ __forceinline__ double val(const Sum& a) { return a; }
+  static __device__ __forceinline__ Sum zero() { return 0.0; }
+};
+template <> struct Num<float> {
+  using Sum = FF;
+  static __device__ __forceinline__ void add(Sum& a, const Sum& b) { ff_add(a, b); }
+  static __device__ __forceinline__ void sub(Sum& a, const Sum& b) {
+    ff_add(a, -b.hi);
+    a.lo -= b.lo;
+  }
+  static __device__ __forceinline__ double val(const Sum& a) { return (double)a.hi + (double)a.lo; }
+  static __device__ __forceinline__ Sum zero() { return FF{}; }
+};
+
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ double sum() const { return s; }
+};
+template <> struct Acc<float> {
+  float r = 0.f;
+  FF s;
+  __device__ __forceinline__ void add(float v) { r += v; }
+  __device__ __forceinline__ void flush() {
+    ff_add(s, r);
+    r = 0.f;
+  }
+  __device__ __forceinline__ FF sum() const {
+    FF t = s;
+    ff_add(t, r);
+    return t;
+  }
+};
+constexpr int kGainRun = 16;
+constexpr int kLossRun = 32;
+
 // Shared-memory carve-up for nmax bins and S species (T = pair-arithmetic type).
-// Sums are held in FP64 in both forms: the FP32 form adds short runs of pair terms in FP32
-// and folds each run into an FP64 total (see Acc).
 template <typename T>
 struct Smem {
+  using Sum = typename Num<T>::Sum;
   double* M;      // [S][nmax] FP64 state
   double* loss;   // [S][nmax] R, then loss
-  double* stay;   // [S*S][nmax]
-  double* up;     // [S*S][nmax]
+  Sum* stay;      // [S*S][nmax] per-orientation partial gains of bin k
+  Sum* up;        // [S*S][nmax] per-orientation fluxes from bin k to k+1
   T* Mt;          // [S][nmax] state in T (aliases M when T = double)
   T* N;           // [S][nmax]
   T* lam;         // [S][nmax]
   T* xs;          // [nmax]
+  int* lim;       // [S*nmax] rows whose limiter ratio is below 1, ascending
   static __host__ __device__ size_t bytes(int nmax, int S) {
-    size_t b = sizeof(double) * (2 * S * nmax + 2 * S * S * nmax);
+    size_t b = sizeof(double) * 2 * S * nmax + sizeof(Sum) * 2 * S * S * nmax;
     if (sizeof(T) != sizeof(double)) b += sizeof(T) * S * nmax;
-    b += sizeof(T) * (2 * S * nmax + nmax);
+    b += sizeof(T) * (2 * S * nmax + nmax) + sizeof(int) * S * nmax;
     return (b + 15) & ~size_t(15);
   }
   __device__ void carve(unsigned char* base, int nmax, int S) {
@@ -147,10 +253,10 @@ struct Smem {
     p += sizeof(double) * S * nmax;
     loss = reinterpret_cast<double*>(p);
     p += sizeof(double) * S * nmax;
-    stay = reinterpret_cast<double*>(p);
-    p += sizeof(double) * S * S * nmax;
-    up = reinterpret_cast<double*>(p);
-    p += sizeof(double) * S * S * nmax;
+    stay = reinterpret_cast<Sum*>(p);
+    p += sizeof(Sum) * S * S * nmax;
+    up = reinterpret_cast<Sum*>(p);
+    p += sizeof(Sum) * S * S * nmax;
     if (sizeof(T) != sizeof(double)) {
       Mt = reinterpret_cast<T*>(p);
       p += sizeof(T) * S * nmax;
@@ -162,36 +268,90 @@ struct Smem {
     lam = reinterpret_cast<T*>(p);
     p += sizeof(T) * S * nmax;
     xs = reinterpret_cast<T*>(p);
+    p += sizeof(T) * nmax;
+    lim = reinterpret_cast<int*>(p);
   }
 };
 
-// Running sum of pair terms: FP64 adds each term; FP32 adds a run of terms in FP32 and
-// folds the run into an FP64 total at flush(), so rounding grows with the run length (16 or
-// 32 terms), not with the full sum over a few hundred bins.
-template <typename T> struct Acc;
-template <> struct Acc<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double v) { s += v; }
-  __device__ __forceinline__ void flush() {}
-  __device__ __forceinline__ double total() const { return s; }
+// Bott's flux with target-bin constants hoisted out of the pair loop. When bin k+1 holds at
+// least 1e-30 of the largest content bin k can reach (Mk + 2B), ln(rho + 1e-60) equals
+// ln M_{k+1} - ln g to 1e-30, so the per-pair work is one logarithm, one exponential (which
+// also gives e^y - 1 without cancellation), a reciprocal square root and a reciprocal, all
+// table-driven or Newton-refined. Otherwise (bin k+1 empty or nearly so) the direct form
+// above is used.
+struct TargetFP64 {
+  double Mk, Mk1, lnMk1, sqMk1;
+  bool fast;
 };
-template <> struct Acc<float> {
-  float r = 0.f;
-  double s = 0.0;
-  __device__ __forceinline__ void add(float v) { r += v; }
-  __device__ __forceinline__ void flush() {
-    s += (double)r;
-    r = 0.f;
+__device__ __forceinline__ TargetFP64 target_fp64(double Mk, double Mk1, double B, const MathTabs& mt) {
+  TargetFP64 tg;
+  tg.Mk = Mk;
+  tg.Mk1 = Mk1;
+  tg.fast = Mk1 >= 1e-30 * (Mk + 2.0 * B) && Mk1 >= 1e-300;
+  tg.lnMk1 = tg.fast ? fsbm_log(Mk1, mt) : 0.0;
+  tg.sqMk1 = tg.fast ? sqrt(Mk1) : 0.0;
+  return tg;
+}
+// 1 / sqrt(x) for normal x > 0: the SFU's approximation refined by two Newton steps
+// y <- y + y (1 - x y^2) / 2 (each step squares the relative error).
+__device__ __forceinline__ double fsbm_rsqrt(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-(x * y), y, 1.0);
+    y = fma(0.5 * y, e, y);
   }
-  __device__ __forceinline__ double total() const { return s + (double)r; }
-};
-constexpr int kGainRun = 16;
-constexpr int kLossRun = 32;
+  return y;
+}
+// 1 / x for normal x != 0: SFU approximation and two Newton steps y <- y + y (1 - x y).
+__device__ __forceinline__ double fsbm_rcp(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = fma(y, fma(-x, y, 1.0), y);
+  return y;
+}
+// F for one pair: e^{x1/2} = sqrt(M_{k+1}) / sqrt(g), e^{-c x1} - 1 from the table
+// exponential, x1 = ln M_{k+1} - ln g. F >= 0 holds exactly (the factors' signs agree), so
+// only the upper clip is needed.
+__device__ __forceinline__ double bott_flux_fast(double dM, const TargetFP64& tg, double c, const MathTabs& mt) {
+  const double g = tg.Mk + dM;
+  if (!tg.fast || !(g >= 1e-300)) return bott_flux(dM, tg.Mk, tg.Mk1, c);
+  const double x1 = tg.lnMk1 - fsbm_log(g, mt);
+  if (x1 == 0.0) return fmin(dM * c, dM);
+  const double A = tg.sqMk1 * fsbm_rsqrt(g);
+  double E, em1;
+  fsbm_exp_em1(-c * x1, mt, &E, &em1);
+  return fmin((dM * A) * (-em1) * fsbm_rcp(x1), dM);
+}
 
-// Gain pass for one (orientation, block of 32 target bins) warp task.
+// Flux of one pair into a regular target bin (precision-specific target constants).
+template <typename T> struct TargetOf;
+template <> struct TargetOf<double> {
+  TargetFP64 tg;
+  __device__ __forceinline__ void init(double Mk, double Mk1, double B, const MathTabs& mt) {
+    tg = target_fp64(Mk, Mk1, B, mt);
+  }
+  __device__ __forceinline__ double flux(double dM, double c, const MathTabs& mt) const {
+    return bott_flux_fast(dM, tg, c, mt);
+  }
+};
+template <> struct TargetOf<float> {
+  float Mk, Mk1;
+  __device__ __forceinline__ void init(float mk, float mk1, double, const MathTabs&) {
+    Mk = mk;
+    Mk1 = mk1;
+  }
+  __device__ __forceinline__ float flux(float dM, float c, const MathTabs&) const {
+    return bott_flux_f32(dM, Mk, Mk1, c);
+  }
+};
+
 template <typename T, bool LIMITED>
-__device__ __forceinline__ void gain_task(const GridDev& G, const Smem<T>& sm, const Orient& o, const int* lo,
-                                          const int* hi, int k, T dt, double* out_stay, double* out_up) {
+__device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T>& sm, const Orient& o,
+                                          const int* lo, const int* hi, int k, T dt, double B, const MathTabs& mt,
+                                          typename Num<T>::Sum* out_stay, typename Num<T>::Sum* out_up) {
   const int n = G.n;
   Acc<T> stay, up;
   if (k >= 1 && k < n) {
@@ -199,14 +359,15 @@ __device__ __forceinline__ void gain_task(const GridDev& G, const Smem<T>& sm, c
     const T* __restrict__ cd = Sel<T>::cd(G);
     const T* Ns = sm.N + o.s * n;
     const T* Nl = sm.N + o.l * n;
+    const T* Ms = sm.Mt + o.s * n;
     const T* Ls = sm.lam + o.s * n;
     const T* Ll = sm.lam + o.l * n;
     const int lo_s = lo[o.s], hi_s = hi[o.s], lo_l = lo[o.l], hi_l = hi[o.l];
     const bool top = (k == n - 1);
     // regular target: pairs with m + kappa[d] == k; top bin: every pair with m + kappa[d] >= n-1
     // stays there without a flux
-    const T Mk = top ? T(0) : sm.Mt[o.c * n + k];
-    const T Mk1 = top ? T(0) : sm.Mt[o.c * n + k + 1];
+    TargetOf<T> tgt;
+    tgt.init(top ? T(0) : sm.Mt[o.c * n + k], top ? T(0) : sm.Mt[o.c * n + k + 1], B, mt);
     for (int kap = 0; kap <= G.kappa_max; ++kap) {
       const int mlo = top ? max(n - 1 - kap, lo_l) : max(k - kap, lo_l);
       const int mhi = top ? min(n - 1, hi_l) : min(k - kap, hi_l);
@@ -220,18 +381,14 @@ __device__ __forceinline__ void gain_task(const GridDev& G, const Smem<T>& sm, c
           const int r1 = min(d1, r0 + kGainRun - 1);
           for (int d = r0; d <= r1; ++d) {
             const int i = m - d;
-            T C = __ldg(Kd + (size_t)d * n + m) * Ns[i] * nl;
-            if (LIMITED) C *= (Ls[i] < ll ? Ls[i] : ll);
-            if (o.half && d == 0) C *= T(0.5);
-            const T dM = C * (sm.xs[i] + xl);
+            // dM = C (x_i + x_m) = K N_m dt (M_i + N_i x_m)
+            T dM = __ldg(Kd + ((size_t)d * n + m) * S2) * nl * fma(Ns[i], xl, Ms[i]);
+            if (LIMITED) dM *= (Ls[i] < ll ? Ls[i] : ll);
+            if (o.half && d == 0) dM *= T(0.5);
             if (dM > T(0)) {
-              if (top) {
-                stay.add(dM);
-              } else {
-                const T F = bott_flux(dM, Mk, Mk1, __ldg(cd + d));
-                stay.add(dM - F);
-                up.add(F);
-              }
+              const T c = __ldg(cd + d);
+              stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
+              if (!top && c != T(0)) up.add(tgt.flux(dM, c, mt));  // no flux out of the top bin; c = 0: F = 0
             }
           }
           stay.flush();
@@ -240,8 +397,10 @@ __device__ __forceinline__ void gain_task(const GridDev& G, const Smem<T>& sm, c
       }
     }
   }
-  *out_stay = stay.total();
-  *out_up = up.total();
+  typename Num<T>::Sum st = stay.sum(), u = up.sum();
+  Num<T>::sub(st, u);
+  *out_stay = st;
+  *out_up = u;
 }
 
 template <typename T>
@@ -256,6 +415,8 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
   __shared__ Orient ori[kMaxOrient];
   __shared__ int s_lo[kMaxSpecies], s_hi[kMaxSpecies], s_sp[kMaxSpecies];
   __shared__ int s_next;
+  __shared__ int s_task;
+  __shared__ int s_nlim;
 
   const int S = t.S;
   Smem<T> sm;
@@ -315,19 +476,17 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
     // orientation list: same species once; each cross pair in both index orders
     if (tid == 0) {
       int q = 0;
-      const size_t nn = (size_t)n * n;
       for (int a = 0; a < ns; ++a)
         for (int b = a; b < ns; ++b) {
           const int ia = s_sp[a], ib = s_sp[b];
           const int prod = t.product[ia * S + ib];
           const int cs = (prod == ia) ? a : b;
-          ori[q++] = Orient{(int8_t)a, (int8_t)b, 0, (int8_t)(a == b), (int8_t)cs, (int)((ia * S + ib) * nn)};
-          if (a != b) ori[q++] = Orient{(int8_t)b, (int8_t)a, 1, 0, (int8_t)cs, (int)((ib * S + ia) * nn)};
+          ori[q++] = Orient{(int8_t)a, (int8_t)b, 0, (int8_t)(a == b), (int8_t)cs, ia * S + ib};
+          if (a != b) ori[q++] = Orient{(int8_t)b, (int8_t)a, 1, 0, (int8_t)cs, ib * S + ia};
         }
     }
     __syncthreads();
     const int O = ns * ns;
-    const int nkb = (n + 31) >> 5;
 
     int status = 0;
     double emax = 0.0;
@@ -365,7 +524,7 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
       }
       __syncthreads();
 
-      // 2. requested loss and limiter ratios
+      // 2. requested loss R and limiter ratios (one lane per row (a, i); Kr is i-fastest)
       const T* __restrict__ Kr = Sel<T>::Kr(G);
       bool fired = false;
       for (int r = tid; r < E; r += NT) {
@@ -383,8 +542,8 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
               acc.flush();
             }
           }
-          R = dt * sm.M[r] * acc.total();
-          if (R > 0.0 && sm.M[r] / R < 1.0) {
+          R = dt * sm.M[r] * Num<T>::val(acc.sum());
+          if (R > sm.M[r]) {  // lambda = M / R < 1 (R > 0 here)
             lamd = sm.M[r] / R;
             fired = true;
           }
@@ -392,46 +551,85 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
         sm.loss[r] = R;
         sm.lam[r] = (T)lamd;
       }
+      if (tid == 0) s_task = 0;
       const bool limited = __syncthreads_or(fired);
       if (limited) status |= 1;
 
-      // 3. limited losses
+      // 3. limited losses: loss_i = dt M_i sum_j K N_j min(lam_i, lam_j)
+      //      = lam_i R_i - dt M_i sum_{j: lam_j < lam_i} (lam_i - lam_j) K N_j,
+      //    where lam_i R_i = M_i when lam_i < 1, and the correction runs only over the rows
+      //    whose ratio fired, listed in ascending order (a fixed summation order).
       if (limited) {
+        if (warp == 0) {
+          int cnt = 0;
+          for (int r0 = 0; r0 < E; r0 += 32) {
+            const int r = r0 + lane;
+            const bool f = r < E && sm.lam[r] < T(1);
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (f) sm.lim[cnt + __popc(bal & ((1u << lane) - 1u))] = r;
+            cnt += __popc(bal);
+          }
+          if (lane == 0) s_nlim = cnt;
+        }
+        __syncthreads();
+        const int L = s_nlim;
         for (int r = tid; r < E; r += NT) {
           const int a = r / n, i = r - a * n;
           if (i < s_lo[a] || i > s_hi[a]) continue;
           const T li = sm.lam[r];
           Acc<T> acc;
-          for (int b = 0; b < ns; ++b) {
-            const T* Kab = Kr + (size_t)(s_sp[a] * S + s_sp[b]) * n * n + i;
-            const T* Nb = sm.N + b * n;
-            const T* Lb = sm.lam + b * n;
-            for (int j0 = s_lo[b]; j0 <= s_hi[b]; j0 += kLossRun) {
-              const int j1 = min(s_hi[b], j0 + kLossRun - 1);
-              for (int j = j0; j <= j1; ++j) {
-                const T phi = Lb[j] < li ? Lb[j] : li;
-                acc.add(__ldg(Kab + (size_t)j * n) * Nb[j] * phi);
+          for (int q0 = 0; q0 < L; q0 += kLossRun) {
+            const int q1 = min(L, q0 + kLossRun);
+            for (int q = q0; q < q1; ++q) {
+              const int rj = sm.lim[q];
+              const T lj = sm.lam[rj];
+              if (lj < li) {
+                const int b = rj / n, j = rj - b * n;
+                const T Kv = __ldg(Kr + (size_t)(s_sp[a] * S + s_sp[b]) * n * n + (size_t)j * n + i);
+                acc.add((li - lj) * Kv * sm.N[rj]);
               }
-              acc.flush();
             }
+            acc.flush();
           }
-          sm.loss[r] = dt * sm.M[r] * acc.total();
+          const double base = li < T(1) ? sm.M[r] : sm.loss[r];
+          sm.loss[r] = base - dt * sm.M[r] * Num<T>::val(acc.sum());
         }
       }
 
-      // 4. gains
-      for (int task = warp; task < O * nkb; task += nw) {
-        const int oi = task / nkb, kb = task - oi * nkb;
-        const int k = kb * 32 + lane;
-        double st_, up_;
-        if (limited)
-          gain_task<T, true>(G, sm, ori[oi], s_lo, s_hi, k, dtT, &st_, &up_);
-        else
-          gain_task<T, false>(G, sm, ori[oi], s_lo, s_hi, k, dtT, &st_, &up_);
-        if (k < n) {
-          sm.stay[oi * n + k] = st_;
-          sm.up[oi * n + k] = up_;
+      // 4. gains. Lanes run over the flattened list of (target bin 1..n-1, orientation)
+      //    items, orientation fastest: a warp covers about 32/O consecutive targets, whose
+      //    distance ranges differ by a few steps at most, so nearly every lane stays busy,
+      //    and the lanes of one (d, m) read one contiguous run of Kd. Warp tasks go out in
+      //    serpentine order, which balances the per-target cost growing with k.
+      {
+        const int n_items = (n - 1) * O;
+        const int n_tasks = (n_items + 31) >> 5;
+        for (;;) {
+          // warps claim tasks costliest first (the cost grows with the target bin)
+          int q = 0;
+          if (lane == 0) q = atomicAdd(&s_task, 1);
+          q = __shfl_sync(0xffffffffu, q, 0);
+          if (q >= n_tasks) break;
+          q = n_tasks - 1 - q;
+          const int f = q * 32 + lane;
+          const bool on = f < n_items;
+          const int kq = on ? f / O : 0;
+          const int ol = on ? f - kq * O : 0;
+          const int k = on ? kq + 1 : 0;
+          typename Num<T>::Sum st_, up_;
+          if (limited)
+            gain_task<T, true>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, &st_, &up_);
+          else
+            gain_task<T, false>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, &st_, &up_);
+          if (on) {
+            sm.stay[ol * n + k] = st_;
+            sm.up[ol * n + k] = up_;
+          }
         }
+      }
+      if (tid < O) {  // bin 0 of every orientation receives nothing
+        sm.stay[tid * n] = Num<T>::zero();
+        sm.up[tid * n] = Num<T>::zero();
       }
       __syncthreads();
 
@@ -439,13 +637,13 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
       double pre = 0.0, post = 0.0;
       for (int e = tid; e < E; e += NT) {
         const int c = e / n, k = e - c * n;
-        double gsum = 0.0;
+        typename Num<T>::Sum gsum = Num<T>::zero();
         for (int q = 0; q < O; ++q) {
           if (ori[q].c != c) continue;
-          gsum += sm.stay[q * n + k];
-          if (k > 0) gsum += sm.up[q * n + k - 1];
+          Num<T>::add(gsum, sm.stay[q * n + k]);
+          if (k > 0) Num<T>::add(gsum, sm.up[q * n + k - 1]);
         }
-        double v = sm.M[e] - sm.loss[e] + gsum;
+        double v = sm.M[e] - sm.loss[e] + Num<T>::val(gsum);
         pre += v;
         if (v < 0.0) v = 0.0;
         post += v;
@@ -488,6 +686,58 @@ cudaError_t plan_t(const Tables& t, int block_dim, int n_sms, CoalLaunch* out) {
 }
 
 }  // namespace
+
+namespace {
+__global__ void k_math_check(MathTabs mt, double* out) {
+  // sweep: log over [1e-300, 1e300] geometrically, exp/expm1 over [-700, 700] and densely near 0
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = gridDim.x * blockDim.x;
+  double el = 0.0, ee = 0.0, em = 0.0;
+  for (int q = tid; q < (1 << 20); q += n) {
+    const double u = (q + 0.5) / (double)(1 << 20);
+    const double x = exp((u - 0.5) * 1381.0);            // 1e-300 .. 1e300
+    const double rl = log(x);
+    el = fmax(el, fabs(fsbm_log(x, mt) - rl) / fmax(fabs(rl), 1e-300));
+    const double y = (u - 0.5) * 1400.0;
+    double ex, e1;
+    fsbm_exp_em1(y, mt, &ex, &e1);
+    ee = fmax(ee, fabs(ex - exp(y)) / exp(y));
+    const double ys = (u - 0.5) * 1e-3 * ((q & 7) + 1);
+    fsbm_exp_em1(ys, mt, &ex, &e1);
+    const double r1 = expm1(ys);
+    if (r1 != 0.0) em = fmax(em, fabs(e1 - r1) / fabs(r1));
+    fsbm_exp_em1(y * 1e-2, mt, &ex, &e1);
+    const double r2 = expm1(y * 1e-2);
+    if (r2 != 0.0) em = fmax(em, fabs(e1 - r2) / fabs(r2));
+  }
+  __shared__ double red[3][256];
+  red[0][threadIdx.x] = el;
+  red[1][threadIdx.x] = ee;
+  red[2][threadIdx.x] = em;
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double m = 0.0;
+    for (int i = 0; i < blockDim.x; ++i) m = fmax(m, red[threadIdx.x][i]);
+    // blocks combine through a CAS-free max on the bit pattern (non-negative doubles order
+    // like their bit patterns)
+    atomicMax(reinterpret_cast<unsigned long long*>(out) + threadIdx.x,
+              (unsigned long long)__double_as_longlong(m));
+  }
+}
+}  // namespace
+
+cudaError_t launch_math_check(const Tables& t, double* out, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 3 * sizeof(double), stream);
+  if (e != cudaSuccess) return e;
+  k_math_check<<<64, 256, 0, stream>>>(t.math, out);
+  return cudaGetLastError();
+}
+
+size_t coal_smem_bytes(const Tables& t, int precision) {
+  int nmax = 0;
+  for (int g = 0; g < t.G; ++g) nmax = t.g[g].n > nmax ? t.g[g].n : nmax;
+  return precision == 0 ? Smem<double>::bytes(nmax, t.S) : Smem<float>::bytes(nmax, t.S);
+}
 
 cudaError_t coal_plan(const Tables& t, int precision, int block_dim, int n_sms, CoalLaunch* out) {
   return precision == 0 ? plan_t<double>(t, block_dim, n_sms, out) : plan_t<float>(t, block_dim, n_sms, out);

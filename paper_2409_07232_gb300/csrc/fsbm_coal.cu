@@ -38,6 +38,7 @@ struct fsbm_coal_ctx {
   bool plan_valid = false;
   // CUDA graph of the last argument set
   bool graph_enabled = false;
+  cudaStream_t cap_stream = nullptr;  // private stream the launch sequence is captured on
   cudaGraphExec_t gexec = nullptr;
   PointsDev g_points{};
   int64_t g_n = -1;
@@ -120,6 +121,10 @@ void pair_offsets(int n, double alpha, std::vector<int>& kap, std::vector<double
 fsbm_status ensure_scratch(fsbm_coal_ctx* c, int64_t n_points) {
   const int64_t nblk = (n_points + kCompactThreads - 1) / kCompactThreads;
   if (n_points > c->cap_points) {
+    if (c->gexec) {  // a captured graph refers to the old scratch buffers
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
     if (c->scratch.block_counts) cudaFree(c->scratch.block_counts);
     if (c->scratch.active_list) cudaFree(c->scratch.active_list);
     if (c->scratch.counters) cudaFree(c->scratch.counters);
@@ -186,7 +191,8 @@ fsbm_status take_events(fsbm_coal_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* o
 
 fsbm_status enqueue(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps,
                     const CoalLaunch& plan, bool capturing) {
-  CU(c, launch_compact(c->t, p, n_points, c->scratch, c->stream));
+  cudaStream_t stream = capturing ? c->cap_stream : c->stream;
+  CU(c, launch_compact(c->t, p, n_points, c->scratch, stream));
   const bool timed = c->timing && !capturing;
   std::pair<cudaEvent_t, cudaEvent_t> ev{};
   if (timed) {
@@ -194,7 +200,7 @@ fsbm_status enqueue(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, doub
     if (st != FSBM_OK) return st;
     CU(c, cudaEventRecord(ev.first, c->stream));
   }
-  CU(c, launch_coal(c->t, c->precision, p, c->scratch, dt, n_steps, plan, c->stream));
+  CU(c, launch_coal(c->t, c->precision, p, c->scratch, dt, n_steps, plan, stream));
   if (timed) {
     CU(c, cudaEventRecord(ev.second, c->stream));
     c->ev_coal.push_back(ev);
@@ -237,10 +243,13 @@ fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, 
       cudaGraphExecDestroy(c->gexec);
       c->gexec = nullptr;
     }
-    CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    // capture on the context's own stream (the caller's may be the legacy default stream,
+    // which cannot be captured); the graph then runs on the caller's stream
+    if (!c->cap_stream) CU(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CU(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     fsbm_status est = enqueue(c, p, n_points, dt, n_steps, c->plan, true);
     cudaGraph_t graph = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+    cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
     if (est != FSBM_OK) {
       if (graph) cudaGraphDestroy(graph);
       return est;
@@ -341,12 +350,14 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
     }
     std::vector<double> x(n), Kd((size_t)S * S * nn, 0.0), Kr((size_t)S * S * nn, 0.0);
     for (int k = 0; k < n; ++k) x[k] = x0 * std::pow(al, (double)k);
+    const int S2 = S * S;
     for (int s = 0; s < S; ++s)
       for (int l = 0; l < S; ++l) {
-        double* kd = Kd.data() + (size_t)(s * S + l) * nn;
         double* kr = Kr.data() + (size_t)(s * S + l) * nn;
+        // Kd[d][m][s*S+l]: the orientations of one (d, m) sit side by side
         for (int d = 0; d < n; ++d)
-          for (int m = d; m < n; ++m) kd[(size_t)d * n + m] = kern_entry(Kg, S, n, s, m - d, l, m);
+          for (int m = d; m < n; ++m)
+            Kd[((size_t)d * n + m) * S2 + (s * S + l)] = kern_entry(Kg, S, n, s, m - d, l, m);
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) kr[(size_t)j * n + i] = kern_entry(Kg, S, n, s, i, l, j);
       }
@@ -359,6 +370,44 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
         (st = upload(c, Kr, &gd.Kr64)) != FSBM_OK || (st = upload(c, Kr32, &gd.Kr32)) != FSBM_OK)
       return bail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(FSBM_E_CUDA);
+  }
+  {
+    // one point's spectra, sums and partial gains live in shared memory: refuse grids whose
+    // working set (about 8 (2 S + 2 S^2) n + (2 or 3) S n w bytes) exceeds the device's
+    // per-CTA limit (about 400 bins with 5 species on GB300)
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess)
+      return bail(FSBM_E_CUDA);
+    if (coal_smem_bytes(c->t, c->precision) + 1024 > (size_t)optin) return bail(FSBM_E_UNSUPPORTED);
+  }
+  {
+    // tables of the FP64 logarithm and exponential (Tang's table-driven methods), in long double
+    std::vector<double> lt(2 * kLogTab), et(2 * kExpTab);
+    for (int t = 0; t < kLogTab; ++t) {
+      const long double F = 1.0L + (long double)(t + kLogTabLo) / 256.0L;
+      lt[2 * t] = (double)(1.0L / F);
+      lt[2 * t + 1] = (double)logl(F);
+    }
+    for (int j = 0; j < kExpTab; ++j) {
+      const long double v = exp2l((long double)j / 64.0L);
+      et[2 * j] = (double)v;
+      et[2 * j + 1] = (double)(v - (long double)et[2 * j]);
+    }
+    fsbm_status st;
+    if ((st = upload(c, lt, &c->t.math.logtab)) != FSBM_OK || (st = upload(c, et, &c->t.math.exptab)) != FSBM_OK)
+      return bail(st);
+    const long double ln2 = logl(2.0L);
+    uint64_t bits;
+    const double ln2d = (double)ln2;
+    std::memcpy(&bits, &ln2d, sizeof bits);
+    bits &= ~uint64_t(0xffffffffu);  // clear 32 low mantissa bits: e * hi exact for |e| < 2^11
+    double hi;
+    std::memcpy(&hi, &bits, sizeof hi);
+    c->t.math.ln2_hi = hi;
+    c->t.math.ln2_lo = (double)(ln2 - (long double)hi);
+    c->t.math.l64_hi = hi / 64.0;
+    c->t.math.l64_lo = c->t.math.ln2_lo / 64.0;
+    c->t.math.inv_l64 = (double)(64.0L / ln2);
   }
   std::stable_sort(cls.begin(), cls.end(), [](const Cls& a, const Cls& b) { return a.cost > b.cost; });
   std::memset(c->t.bucket_rank, -1, sizeof(c->t.bucket_rank));
@@ -586,6 +635,7 @@ fsbm_status fsbm_coal_destroy(fsbm_coal_ctx* c) {
   if (!c) return FSBM_OK;
   cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void* p : c->table_allocs) cudaFree(p);
   if (c->scratch.block_counts) cudaFree(c->scratch.block_counts);
   if (c->scratch.active_list) cudaFree(c->scratch.active_list);
@@ -596,6 +646,18 @@ fsbm_status fsbm_coal_destroy(fsbm_coal_ctx* c) {
   for (auto& ev : c->ev_step) c->ev_pool.insert(c->ev_pool.end(), {ev.first, ev.second});
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
+  return FSBM_OK;
+}
+
+fsbm_status fsbm_coal_math_check(fsbm_coal_ctx* c, double* out3) {
+  if (!c || !out3) return FSBM_E_ARG;
+  double* d = nullptr;
+  CU(c, cudaMalloc(&d, 3 * sizeof(double)));
+  cudaError_t e = launch_math_check(c->t, d, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out3, d, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fsbm_coal_math_check");
   return FSBM_OK;
 }
 

@@ -7,13 +7,16 @@
 //                     with c = ((1 + alpha^-d) alpha^-kappa - 1) / (alpha - 1), so both
 //                     depend on d only (the pair tables of Sec. V-A shrink to length n).
 //   x[k]              bin masses.
-//   Kd[s][l][d][m]    kernel of species s bin m-d with species l bin m (m fastest): the
-//                     layout the gain pass walks, one lane per target bin, d in lock-step.
+//   Kd[d][m][s*S+l]   kernel of species s bin m-d with species l bin m, the S*S ordered
+//                     species pairs innermost: the gain pass puts one lane per species
+//                     orientation on the same (d, m), so a warp's loads are contiguous.
 //   Kr[a][b][j][i]    kernel of species a bin i with species b bin j (i fastest): the
 //                     layout of the loss mat-vec, one lane per row i.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "fsbm_math.cuh"
 
 namespace fsbm {
 
@@ -52,6 +55,7 @@ struct Tables {
   int8_t product[kMaxSpecies * kMaxSpecies];
   int8_t bucket_rank[kMaxGrids * (kMaxSpecies + 1)];  // [g][n stored species] -> LPT rank
   GridDev g[kMaxGrids];
+  MathTabs math;
 };
 
 // Caller-owned per-point arrays (device pointers).
@@ -87,8 +91,12 @@ struct CoalLaunch {
   int grid_dim;
   size_t smem;
 };
+size_t coal_smem_bytes(const Tables& t, int precision);  // dynamic shared memory of one CTA
 cudaError_t coal_plan(const Tables& t, int precision, int block_dim, int n_sms, CoalLaunch* out);
 cudaError_t launch_coal(const Tables& t, int precision, const PointsDev& p, const Scratch& s, double dt,
                         int n_steps, const CoalLaunch& plan, cudaStream_t stream);
+// Largest relative errors of fsbm_log, fsbm_exp and the e^y - 1 of fsbm_exp_em1 against
+// CUDA's log, exp and expm1 over a fixed sweep of arguments (written to out[0..2] on device).
+cudaError_t launch_math_check(const Tables& t, double* out, cudaStream_t stream);
 
 }  // namespace fsbm
