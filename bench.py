@@ -219,6 +219,7 @@ def run_form(pkg, torch, w, precision, steps, warmup, graph=False):
     """Time one form on one workload; returns a dict with value, kernel time and work."""
     with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
         ds = fc.upload(w.state(copy=False))
+        fc.autotune(ds)
         fc.set_graph(graph)
         fc.set_timing(True)
         ms, st = time_steps(fc, ds, w, steps, warmup, fc.stream, torch)
@@ -244,7 +245,7 @@ def pairs_per_active(w):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["conus", "stress", "ragged"], default="conus")
@@ -284,6 +285,7 @@ def main():
 
     with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
         ds = fc.upload(w.state(copy=False))
+        fc.autotune(ds)  # picks the CTA size on a copy of a sample of the batch
         fc.set_timing(True)
         with Clocks(local) as clk:
             ms, st = time_steps(fc, ds, w, args.steps, args.warmup, fc.stream, torch, barrier)
@@ -346,6 +348,7 @@ def main():
         "e2e": {"value": units / e2e_max, "unit": "grid-point coal updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 4 * args.steps,
+        "block_dim": st["block_dim"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_coal<%s>" % ("double" if precision == 0 else "float"),

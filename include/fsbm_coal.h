@@ -177,10 +177,11 @@ FSBM_API fsbm_status fsbm_coal_get_stats(fsbm_coal_ctx* ctx, fsbm_coal_stats* ou
  * count (which may exceed cap; then only cap entries are written). */
 FSBM_API fsbm_status fsbm_coal_get_active_list(fsbm_coal_ctx* ctx, int32_t* out, int64_t cap, int64_t* n_out);
 
-/* Self-check of the library's FP64 logarithm and exponential (used by the FP64 pair flux)
- * against CUDA's log, exp and expm1 over a fixed sweep of arguments: out3[0..2] receive the
- * largest relative errors of log, exp and e^y - 1. Synchronous; allocates 24 bytes. */
-FSBM_API fsbm_status fsbm_coal_math_check(fsbm_coal_ctx* ctx, double* out3);
+/* Self-check of the library's FP64 helpers of the FP64 pair flux over a fixed sweep of
+ * arguments, against CUDA's own functions: out5[0..4] receive the largest errors of the
+ * logarithm (absolute; relative where |ln x| > 1), the exponential and e^y - 1 (relative),
+ * and the reciprocal square root and reciprocal (relative). Synchronous; allocates 40 bytes. */
+FSBM_API fsbm_status fsbm_coal_math_check(fsbm_coal_ctx* ctx, double* out5);
 
 /* Free the context and everything it owns. NULL is accepted. */
 FSBM_API fsbm_status fsbm_coal_destroy(fsbm_coal_ctx* ctx);

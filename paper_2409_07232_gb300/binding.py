@@ -216,7 +216,7 @@ def fsbm_coal_get_active_list(ctx, cap: int) -> np.ndarray:
 
 
 def fsbm_coal_math_check(ctx) -> np.ndarray:
-    out = np.zeros(3, np.float64)
+    out = np.zeros(5, np.float64)
     _check(ctx, load().fsbm_coal_math_check(ctx, out.ctypes.data), "fsbm_coal_math_check")
     return out
 

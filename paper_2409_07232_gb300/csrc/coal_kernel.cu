@@ -60,23 +60,6 @@ __device__ __forceinline__ int warp_max_i(int v) {
   return v;
 }
 
-// Deterministic block sum of one value per thread (fixed butterfly + fixed warp order).
-__device__ double block_sum(double v, double* red) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  v = warp_sum(v);
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    double u = lane < nw ? red[lane] : 0.0;
-    u = warp_sum(u);
-    if (lane == 0) red[32] = u;
-  }
-  __syncthreads();
-  const double r = red[32];
-  __syncthreads();
-  return r;
-}
-
 // Bott's flux of mass dM deposited in bin k toward bin k + 1 (see fsbm_coal.h).
 __device__ __forceinline__ double bott_flux(double dM, double Mk, double Mk1, double c) {
   const double g = Mk + dM;
@@ -155,12 +138,14 @@ __device__ __forceinline__ float bott_flux_f32(float dM, float Mk, float Mk1, fl
 template <typename T> struct Sel;
 template <> struct Sel<double> {
   static __device__ const double* x(const GridDev& g) { return g.x64; }
+  static __device__ const double* invx(const GridDev& g) { return g.invx64; }
   static __device__ const double* cd(const GridDev& g) { return g.cd64; }
   static __device__ const double* Kd(const GridDev& g) { return g.Kd64; }
   static __device__ const double* Kr(const GridDev& g) { return g.Kr64; }
 };
 template <> struct Sel<float> {
   static __device__ const float* x(const GridDev& g) { return g.x32; }
+  static __device__ const float* invx(const GridDev& g) { return g.invx32; }
   static __device__ const float* cd(const GridDev& g) { return g.cd32; }
   static __device__ const float* Kd(const GridDev& g) { return g.Kd32; }
   static __device__ const float* Kr(const GridDev& g) { return g.Kr32; }
@@ -292,38 +277,45 @@ __device__ __forceinline__ TargetFP64 target_fp64(double Mk, double Mk1, double 
   tg.sqMk1 = tg.fast ? sqrt(Mk1) : 0.0;
   return tg;
 }
-// 1 / sqrt(x) for normal x > 0: the SFU's approximation refined by two Newton steps
-// y <- y + y (1 - x y^2) / 2 (each step squares the relative error).
+// 1 / sqrt(x) for normal x > 0: the SFU's approximation y (relative error near 2^-20)
+// corrected once to third order: with e = 1 - x y^2, 1/sqrt(x) = y (1 - e)^(-1/2)
+// = y (1 + e/2 + 3e^2/8 + O(e^3)).
 __device__ __forceinline__ double fsbm_rsqrt(double x) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double e = fma(-(x * y), y, 1.0);
-    y = fma(0.5 * y, e, y);
-  }
-  return y;
+  const double e = fma(-(x * y), y, 1.0);
+  return fma(y * e, fma(e, 0.375, 0.5), y);
 }
-// 1 / x for normal x != 0: SFU approximation and two Newton steps y <- y + y (1 - x y).
+// 1 / x for normal x != 0: the SFU's approximation y corrected once to third order:
+// with e = 1 - x y, 1/x = y / (1 - e) = y (1 + e + e^2 + O(e^3)).
 __device__ __forceinline__ double fsbm_rcp(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-#pragma unroll
-  for (int it = 0; it < 2; ++it) y = fma(y, fma(-x, y, 1.0), y);
-  return y;
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+// Sign tests on the bit pattern run on the integer pipes instead of the (slow) FP64 pipe.
+__device__ __forceinline__ bool pos(double v) { return __double_as_longlong(v) > 0; }  // v > 0, v not NaN-negative
+__device__ __forceinline__ bool pos(float v) { return __float_as_int(v) > 0; }
+__device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) << 1) == 0; }
+// min of two non-negative doubles through their bit patterns (they order like integers)
+__device__ __forceinline__ double min_nonneg(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b) ? a : b;
 }
 // F for one pair: e^{x1/2} = sqrt(M_{k+1}) / sqrt(g), e^{-c x1} - 1 from the table
 // exponential, x1 = ln M_{k+1} - ln g. F >= 0 holds exactly (the factors' signs agree), so
 // only the upper clip is needed.
 __device__ __forceinline__ double bott_flux_fast(double dM, const TargetFP64& tg, double c, const MathTabs& mt) {
   const double g = tg.Mk + dM;
-  if (!tg.fast || !(g >= 1e-300)) return bott_flux(dM, tg.Mk, tg.Mk1, c);
+  if (!tg.fast || __double_as_longlong(g) < 0x01a56e1fc2f8f359LL)  // g < 1e-300
+    return bott_flux(dM, tg.Mk, tg.Mk1, c);
   const double x1 = tg.lnMk1 - fsbm_log(g, mt);
-  if (x1 == 0.0) return fmin(dM * c, dM);
+  if (is_zero(x1)) return min_nonneg(dM * c, dM);
   const double A = tg.sqMk1 * fsbm_rsqrt(g);
   double E, em1;
   fsbm_exp_em1(-c * x1, mt, &E, &em1);
-  return fmin((dM * A) * (-em1) * fsbm_rcp(x1), dM);
+  return min_nonneg((dM * A) * (-em1) * fsbm_rcp(x1), dM);
 }
 
 // Flux of one pair into a regular target bin (precision-specific target constants).
@@ -377,20 +369,25 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
         const T nl = Nl[m] * dt;
         const T xl = sm.xs[m];
         const T ll = LIMITED ? Ll[m] : T(1);
-        for (int r0 = d0; r0 <= d1; r0 += kGainRun) {
-          const int r1 = min(d1, r0 + kGainRun - 1);
-          for (int d = r0; d <= r1; ++d) {
-            const int i = m - d;
-            // dM = C (x_i + x_m) = K N_m dt (M_i + N_i x_m)
-            T dM = __ldg(Kd + ((size_t)d * n + m) * S2) * nl * fma(Ns[i], xl, Ms[i]);
-            if (LIMITED) dM *= (Ls[i] < ll ? Ls[i] : ll);
-            if (o.half && d == 0) dM *= T(0.5);
-            if (dM > T(0)) {
-              const T c = __ldg(cd + d);
-              stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
-              if (!top && c != T(0)) up.add(tgt.flux(dM, c, mt));  // no flux out of the top bin; c = 0: F = 0
-            }
+        // one pair (m - d, m): dM = C (x_i + x_m) = K N_m dt (M_i + N_i x_m) h phi
+        auto pair = [&](int d, T h) {
+          const int i = m - d;
+          T dM = __ldg(Kd + ((size_t)d * n + m) * S2) * nl * fma(Ns[i], xl, Ms[i]) * h;
+          if (LIMITED) dM *= (Ls[i] < ll ? Ls[i] : ll);
+          if (pos(dM)) {
+            const T c = __ldg(cd + d);
+            stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
+            if (!top && !is_zero(c)) up.add(tgt.flux(dM, c, mt));  // none out of the top bin; c = 0: F = 0
           }
+        };
+        int dstart = d0;
+        if (o.half && d0 == 0 && d1 >= 0) {  // the same-species diagonal pair counts once: h = 1/2
+          pair(0, T(0.5));
+          dstart = 1;
+        }
+        for (int r0 = dstart; r0 <= d1; r0 += kGainRun) {
+          const int r1 = min(d1, r0 + kGainRun - 1);
+          for (int d = r0; d <= r1; ++d) pair(d, T(1));
           stay.flush();
           up.flush();
         }
@@ -448,12 +445,10 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
     }
     // load the spectrum (FP64 on chip) and the bin masses
     bool bad = false;
-    double part = 0.0;
     for (int e = tid; e < E; e += NT) {
       const double v = (double)spec[e];
       bad |= !(v >= 0.0) || !(v <= DBL_MAX);
       sm.M[e] = v;
-      part += v;
     }
     for (int k = tid; k < n; k += NT) sm.xs[k] = Sel<T>::x(G)[k];
     if (__syncthreads_or(bad)) {
@@ -464,7 +459,16 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
       }
       continue;
     }
-    const double B0 = block_sum(part, red);
+    // the budget, summed by one warp in the order the end-of-step totals use, so that a
+    // step that changes nothing rescales by exactly 1
+    if (warp == 0) {
+      double b = 0.0;
+      for (int e = lane; e < E; e += 32) b += sm.M[e];
+      b = warp_sum(b);
+      if (lane == 0) red[2] = b;
+    }
+    __syncthreads();
+    const double B0 = red[2];
     if (!(B0 > 0.0)) {
       if (tid == 0) {
         pd.status[p] = 4;
@@ -491,10 +495,9 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
     int status = 0;
     double emax = 0.0;
     for (int step = 0; step < n_steps; ++step) {
-      // 1. budget and active ranges
-      double ps = 0.0;
-      for (int e = tid; e < E; e += NT) ps += sm.M[e];
-      const double Bs = block_sum(ps, red);
+      // 1. budget and active ranges. The budget of every step is the point's mass B0: each
+      //    step ends rescaled to it (the start-of-step total equals B0 to rounding).
+      const double Bs = B0;
       for (int a = warp; a < ns; a += nw) {
         const double* Ma = sm.M + a * n;
         double mx = 0.0;
@@ -518,9 +521,9 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
       }
       for (int e = tid; e < E; e += NT) {
         const int k = e % n;
-        const double m = sm.M[e];
-        sm.N[e] = (T)(m / Sel<double>::x(G)[k]);
-        if (sizeof(T) != sizeof(double)) sm.Mt[e] = (T)m;
+        const T m = (T)sm.M[e];
+        sm.N[e] = m * __ldg(Sel<T>::invx(G) + k);  // N = M / x through the table of 1 / x
+        if (sizeof(T) != sizeof(double)) sm.Mt[e] = m;
       }
       __syncthreads();
 
@@ -633,8 +636,8 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
       }
       __syncthreads();
 
-      // 5. update, mass error, clamp, renormalise
-      double pre = 0.0, post = 0.0;
+      // 5. update, mass error, clamp, renormalise (FP64). The pre-clamp values go to `loss`
+      //    (no longer needed) so that one warp forms both totals in a fixed order.
       for (int e = tid; e < E; e += NT) {
         const int c = e / n, k = e - c * n;
         typename Num<T>::Sum gsum = Num<T>::zero();
@@ -643,17 +646,27 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
           Num<T>::add(gsum, sm.stay[q * n + k]);
           if (k > 0) Num<T>::add(gsum, sm.up[q * n + k - 1]);
         }
-        double v = sm.M[e] - sm.loss[e] + Num<T>::val(gsum);
-        pre += v;
-        if (v < 0.0) v = 0.0;
-        post += v;
-        sm.M[e] = v;
+        const double v = sm.M[e] - sm.loss[e] + Num<T>::val(gsum);
+        sm.loss[e] = v;
+        sm.M[e] = v < 0.0 ? 0.0 : v;
       }
-      const double spre = block_sum(pre, red);
-      const double spost = block_sum(post, red);
-      const double err = fabs(spre - Bs) / Bs;
-      emax = fmax(emax, err);
-      const double scale = Bs / spost;
+      __syncthreads();
+      if (warp == 0) {
+        double pre = 0.0, post = 0.0;
+        for (int e = lane; e < E; e += 32) {
+          pre += sm.loss[e];
+          post += sm.M[e];
+        }
+        pre = warp_sum(pre);
+        post = warp_sum(post);
+        if (lane == 0) {
+          red[0] = fabs(pre - Bs) / Bs;
+          red[1] = Bs / post;
+        }
+      }
+      __syncthreads();
+      emax = fmax(emax, red[0]);
+      const double scale = red[1];
       for (int e = tid; e < E; e += NT) sm.M[e] = sm.M[e] * scale;
       __syncthreads();
     }
@@ -692,12 +705,12 @@ __global__ void k_math_check(MathTabs mt, double* out) {
   // sweep: log over [1e-300, 1e300] geometrically, exp/expm1 over [-700, 700] and densely near 0
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = gridDim.x * blockDim.x;
-  double el = 0.0, ee = 0.0, em = 0.0;
+  double el = 0.0, ee = 0.0, em = 0.0, es = 0.0, er = 0.0;
   for (int q = tid; q < (1 << 20); q += n) {
     const double u = (q + 0.5) / (double)(1 << 20);
     const double x = exp((u - 0.5) * 1381.0);            // 1e-300 .. 1e300
     const double rl = log(x);
-    el = fmax(el, fabs(fsbm_log(x, mt) - rl) / fmax(fabs(rl), 1e-300));
+    el = fmax(el, fabs(fsbm_log(x, mt) - rl) / fmax(fabs(rl), 1.0));  // absolute near x = 1
     const double y = (u - 0.5) * 1400.0;
     double ex, e1;
     fsbm_exp_em1(y, mt, &ex, &e1);
@@ -709,13 +722,18 @@ __global__ void k_math_check(MathTabs mt, double* out) {
     fsbm_exp_em1(y * 1e-2, mt, &ex, &e1);
     const double r2 = expm1(y * 1e-2);
     if (r2 != 0.0) em = fmax(em, fabs(e1 - r2) / fabs(r2));
+    es = fmax(es, fabs(fsbm_rsqrt(x) - rsqrt(x)) * sqrt(x));
+    const double xr = (q & 1) ? -x : x;
+    er = fmax(er, fabs(fsbm_rcp(xr) * xr - 1.0));
   }
-  __shared__ double red[3][256];
+  __shared__ double red[5][256];
   red[0][threadIdx.x] = el;
   red[1][threadIdx.x] = ee;
   red[2][threadIdx.x] = em;
+  red[3][threadIdx.x] = es;
+  red[4][threadIdx.x] = er;
   __syncthreads();
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < 5) {
     double m = 0.0;
     for (int i = 0; i < blockDim.x; ++i) m = fmax(m, red[threadIdx.x][i]);
     // blocks combine through a CAS-free max on the bit pattern (non-negative doubles order
@@ -727,7 +745,7 @@ __global__ void k_math_check(MathTabs mt, double* out) {
 }  // namespace
 
 cudaError_t launch_math_check(const Tables& t, double* out, cudaStream_t stream) {
-  cudaError_t e = cudaMemsetAsync(out, 0, 3 * sizeof(double), stream);
+  cudaError_t e = cudaMemsetAsync(out, 0, 5 * sizeof(double), stream);
   if (e != cudaSuccess) return e;
   k_math_check<<<64, 256, 0, stream>>>(t.math, out);
   return cudaGetLastError();

@@ -348,8 +348,11 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
       gd.d_lo[kap[d]] = std::min(gd.d_lo[kap[d]], d);
       gd.d_hi[kap[d]] = std::max(gd.d_hi[kap[d]], d);
     }
-    std::vector<double> x(n), Kd((size_t)S * S * nn, 0.0), Kr((size_t)S * S * nn, 0.0);
-    for (int k = 0; k < n; ++k) x[k] = x0 * std::pow(al, (double)k);
+    std::vector<double> x(n), invx(n), Kd((size_t)S * S * nn, 0.0), Kr((size_t)S * S * nn, 0.0);
+    for (int k = 0; k < n; ++k) {
+      x[k] = x0 * std::pow(al, (double)k);
+      invx[k] = 1.0 / x[k];
+    }
     const int S2 = S * S;
     for (int s = 0; s < S; ++s)
       for (int l = 0; l < S; ++l) {
@@ -361,10 +364,11 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) kr[(size_t)j * n + i] = kern_entry(Kg, S, n, s, i, l, j);
       }
-    std::vector<float> x32(x.begin(), x.end()), cd32(cd.begin(), cd.end()), Kd32(Kd.begin(), Kd.end()),
-        Kr32(Kr.begin(), Kr.end());
+    std::vector<float> x32(x.begin(), x.end()), invx32(invx.begin(), invx.end()), cd32(cd.begin(), cd.end()),
+        Kd32(Kd.begin(), Kd.end()), Kr32(Kr.begin(), Kr.end());
     fsbm_status st;
     if ((st = upload(c, x, &gd.x64)) != FSBM_OK || (st = upload(c, x32, &gd.x32)) != FSBM_OK ||
+        (st = upload(c, invx, &gd.invx64)) != FSBM_OK || (st = upload(c, invx32, &gd.invx32)) != FSBM_OK ||
         (st = upload(c, cd, &gd.cd64)) != FSBM_OK || (st = upload(c, cd32, &gd.cd32)) != FSBM_OK ||
         (st = upload(c, Kd, &gd.Kd64)) != FSBM_OK || (st = upload(c, Kd32, &gd.Kd32)) != FSBM_OK ||
         (st = upload(c, Kr, &gd.Kr64)) != FSBM_OK || (st = upload(c, Kr32, &gd.Kr32)) != FSBM_OK)
@@ -649,12 +653,12 @@ fsbm_status fsbm_coal_destroy(fsbm_coal_ctx* c) {
   return FSBM_OK;
 }
 
-fsbm_status fsbm_coal_math_check(fsbm_coal_ctx* c, double* out3) {
-  if (!c || !out3) return FSBM_E_ARG;
+fsbm_status fsbm_coal_math_check(fsbm_coal_ctx* c, double* out5) {
+  if (!c || !out5) return FSBM_E_ARG;
   double* d = nullptr;
-  CU(c, cudaMalloc(&d, 3 * sizeof(double)));
+  CU(c, cudaMalloc(&d, 5 * sizeof(double)));
   cudaError_t e = launch_math_check(c->t, d, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out3, d, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out5, d, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(c, e, "fsbm_coal_math_check");

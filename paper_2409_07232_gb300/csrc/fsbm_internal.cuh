@@ -39,6 +39,8 @@ struct GridDev {
   int d_hi[kMaxKappa + 1];
   const double* x64;
   const float* x32;
+  const double* invx64;
+  const float* invx32;
   const double* cd64;
   const float* cd32;
   const double* Kd64;
@@ -95,8 +97,9 @@ size_t coal_smem_bytes(const Tables& t, int precision);  // dynamic shared memor
 cudaError_t coal_plan(const Tables& t, int precision, int block_dim, int n_sms, CoalLaunch* out);
 cudaError_t launch_coal(const Tables& t, int precision, const PointsDev& p, const Scratch& s, double dt,
                         int n_steps, const CoalLaunch& plan, cudaStream_t stream);
-// Largest relative errors of fsbm_log, fsbm_exp and the e^y - 1 of fsbm_exp_em1 against
-// CUDA's log, exp and expm1 over a fixed sweep of arguments (written to out[0..2] on device).
+// Largest errors of the FP64 helpers over a fixed sweep of arguments (written to out[0..4] on
+// device): fsbm_log (absolute, relative where |ln x| > 1), fsbm_exp, the e^y - 1 of
+// fsbm_exp_em1 (relative, against CUDA's log, exp, expm1), fsbm_rsqrt and fsbm_rcp (relative).
 cudaError_t launch_math_check(const Tables& t, double* out, cudaStream_t stream);
 
 }  // namespace fsbm
