@@ -43,21 +43,22 @@ import numpy as np  # noqa: E402
 
 # Per-SM unit counts of the GB300 SM (sm_103) used for the ALU roofline.
 SMS = 152
-FP32_LANES = 128            # FP32 FMA per clock per SM
+FP32_LANES = 128            # FP32 FMA-pipe operations per clock per SM
 MUFU_LANES = 16             # special-function (lg2/ex2/rcp/rsq) results per clock per SM
-FP64_PER_CLK = 2            # FP64 FMA per clock per SM (measured 1.73 at 1.9 GHz nominal-clock model)
-# Algorithmic operations of one bin-pair interaction (one unordered pair, one step):
-#  pair flux: C = K N_i N_j dt phi (4 mul + 1 min), dM = C (x_i + x_j) (1 add 1 mul),
-#  g = M_k + dM (1 add), rho = M_{k+1} / g (1 div), x1 = ln(rho) (1 log), e^{x1/2} (1 exp),
-#  expm1(-c x1) (1 exp), F = dM * a * b / x1 (2 mul 1 div), clip (2), accumulate (3 add)
-#  plus the two loss mat-vec passes (R and the limited loss: 2 FMA per ordered pair = 4 per
-#  unordered pair, 2 when the limiter does not fire).
-FP_OPS_PER_PAIR = 18 + 4    # plain FP adds/muls/FMAs/compares (pipe: FMA or FP64)
-MUFU_OPS_PER_PAIR = 5       # 2 divides + 3 transcendentals (FP32: one MUFU op each)
-# FP64 transcendentals and divides run on the FP64 pipe as polynomial/Newton sequences;
-# the algorithmic count takes 8 FP64 ops per divide and 18 per log/exp/expm1 (range
-# reduction + degree-11 polynomial), the cost of a minimal double-precision evaluation.
-FP64_OPS_PER_PAIR = FP_OPS_PER_PAIR + 2 * 8 + 3 * 18
+FP64_PER_CLK = 2            # FP64 operations per clock per SM (the probe measured 1.64-1.73)
+# Algorithmic operations of one bin-pair interaction (one unordered pair, one step) as the
+# method is formulated here (per-target constants hoisted; table-driven FP64 transcendentals
+# after Tang; SFU-seeded reciprocal and square root), counted from the formula, plus the
+# requested-loss mat-vec (2 multiply-adds per unordered pair):
+#  FP32 form: dM 3, sums 2, g 1, rho 1, ln 3, clamp 2, sqrt 1, z 1, test 1,
+#             (1 - e^-z)/z series 12, F and clip 3, mat-vec 2 = 32 FMA-pipe operations,
+#             and 4 SFU operations (reciprocal, log2, reciprocal square root, and one more
+#             in the exponential branch);
+#  FP64 form: dM 3, sums 2, g 1, ln 13, x1 1, e^{x1/2} 6, z 1, e^y - 1 17, F 6,
+#             mat-vec 2 = 52 FP64-pipe operations.
+FP_OPS_PER_PAIR = 32
+MUFU_OPS_PER_PAIR = 4
+FP64_OPS_PER_PAIR = 52
 
 
 def pairs_per_point(n, ns):

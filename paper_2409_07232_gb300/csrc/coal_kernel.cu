@@ -95,8 +95,7 @@ __device__ __forceinline__ float bott_flux(float dM, float Mk, float Mk1, float 
 // m in [1/sqrt2, sqrt2), where the SFU's log2 has an absolute error near 2^-22.6, so ln rho
 // keeps an absolute error near 1e-7 at any magnitude; e^{x1/2} = sqrt(rho) through the SFU
 // reciprocal square root. (1 - e^{-z}) / x1 with z = c x1 is c times the series of
-// (1 - e^{-z}) / z for |z| <= 1/2 (nine terms, relative error below 1e-8), and the direct
-// form otherwise. rho = 0 (empty bin k+1) takes ln rho = ln 1e-60, e^{x1/2} = 1e-30 exactly
+// (1 - e^{-z}) / z for |z| <= 1 (twelve terms), and the direct form otherwise. rho = 0 (empty bin k+1) takes ln rho = ln 1e-60, e^{x1/2} = 1e-30 exactly
 // as the clamped FP32 reading does; subnormal or overflowing ratios use bott_flux above.
 __device__ __forceinline__ float bott_flux_f32(float dM, float Mk, float Mk1, float c) {
   const float g = Mk + dM;
@@ -117,20 +116,25 @@ __device__ __forceinline__ float bott_flux_f32(float dM, float Mk, float Mk1, fl
   }
   const float z = c * x1;
   float ratio;
-  if (fabsf(z) <= 0.5f) {
-    // (1 - e^{-z}) / z = sum_k (-z)^k / (k+1)!, k = 0..8
-    float q = fmaf(z, 1.f / 3628800.f, -1.f / 362880.f);
-    q = fmaf(q, z, 1.f / 40320.f);
-    q = fmaf(q, z, -1.f / 5040.f);
-    q = fmaf(q, z, 1.f / 720.f);
-    q = fmaf(q, z, -1.f / 120.f);
-    q = fmaf(q, z, 1.f / 24.f);
-    q = fmaf(q, z, -1.f / 6.f);
-    q = fmaf(q, z, 0.5f);
-    q = fmaf(q, -z, 1.f);
+  if (fabsf(z) <= 1.f) {
+    // (1 - e^{-z}) / z = sum_k w^k / (k+1)!, w = -z, k = 0..11 (next term below 2e-10)
+    const float w = -z;
+    float q = fmaf(w, 1.f / 479001600.f, 1.f / 39916800.f);
+    q = fmaf(q, w, 1.f / 3628800.f);
+    q = fmaf(q, w, 1.f / 362880.f);
+    q = fmaf(q, w, 1.f / 40320.f);
+    q = fmaf(q, w, 1.f / 5040.f);
+    q = fmaf(q, w, 1.f / 720.f);
+    q = fmaf(q, w, 1.f / 120.f);
+    q = fmaf(q, w, 1.f / 24.f);
+    q = fmaf(q, w, 1.f / 6.f);
+    q = fmaf(q, w, 0.5f);
+    q = fmaf(q, w, 1.f);
     ratio = c * q;
   } else {
-    ratio = __fdividef(1.f - expf(-z), x1);
+    // |z| > 1: e^{-z} from the SFU exponential; 1 - e^{-z} then loses at most a factor
+    // e^{-1} / (1 - e^{-1}) < 0.6 of its relative accuracy
+    ratio = __fdividef(1.f - __expf(-z), x1);
   }
   return fminf(dM * A * ratio, dM);
 }
@@ -258,25 +262,6 @@ struct Smem {
   }
 };
 
-// Bott's flux with target-bin constants hoisted out of the pair loop. When bin k+1 holds at
-// least 1e-30 of the largest content bin k can reach (Mk + 2B), ln(rho + 1e-60) equals
-// ln M_{k+1} - ln g to 1e-30, so the per-pair work is one logarithm, one exponential (which
-// also gives e^y - 1 without cancellation), a reciprocal square root and a reciprocal, all
-// table-driven or Newton-refined. Otherwise (bin k+1 empty or nearly so) the direct form
-// above is used.
-struct TargetFP64 {
-  double Mk, Mk1, lnMk1, sqMk1;
-  bool fast;
-};
-__device__ __forceinline__ TargetFP64 target_fp64(double Mk, double Mk1, double B, const MathTabs& mt) {
-  TargetFP64 tg;
-  tg.Mk = Mk;
-  tg.Mk1 = Mk1;
-  tg.fast = Mk1 >= 1e-30 * (Mk + 2.0 * B) && Mk1 >= 1e-300;
-  tg.lnMk1 = tg.fast ? fsbm_log(Mk1, mt) : 0.0;
-  tg.sqMk1 = tg.fast ? sqrt(Mk1) : 0.0;
-  return tg;
-}
 // 1 / sqrt(x) for normal x > 0: the SFU's approximation y (relative error near 2^-20)
 // corrected once to third order: with e = 1 - x y^2, 1/sqrt(x) = y (1 - e)^(-1/2)
 // = y (1 + e/2 + 3e^2/8 + O(e^3)).
@@ -303,16 +288,49 @@ __device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) << 
 __device__ __forceinline__ double min_nonneg(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b) ? a : b;
 }
-// F for one pair: e^{x1/2} = sqrt(M_{k+1}) / sqrt(g), e^{-c x1} - 1 from the table
-// exponential, x1 = ln M_{k+1} - ln g. F >= 0 holds exactly (the factors' signs agree), so
-// only the upper clip is needed.
+// Bott's flux with target-bin constants hoisted out of the pair loop:
+//  * bin k+1 holds at least 1e-30 of the largest content bin k can reach (Mk + 2B): then
+//    ln(rho + 1e-60) = ln M_{k+1} - ln g to 1e-30 and e^{x1/2} = sqrt(M_{k+1}) / sqrt(g);
+//  * bin k+1 is empty: x1 = ln 1e-60 and e^{x1/2} = 1e-30 for every pair;
+//  * otherwise (a deep tail): x1 = ln(M_{k+1} + 1e-60 g) - ln g and e^{x1/2} =
+//    sqrt(M_{k+1} + 1e-60 g) / sqrt(g).
+// Per pair that is one or two logarithms, one exponential (which also gives e^y - 1 without
+// cancellation), a reciprocal square root and a reciprocal, all table-driven or refined from
+// the SFU's approximations. A sum g below 1e-300 falls back to the direct form above.
+struct TargetFP64 {
+  double Mk, Mk1, lnMk1, sqMk1;
+  int kind;  // 0: regular, 1: bin k+1 empty, 2: deep tail
+};
+__device__ __forceinline__ TargetFP64 target_fp64(double Mk, double Mk1, double B, const MathTabs& mt) {
+  TargetFP64 tg;
+  tg.Mk = Mk;
+  tg.Mk1 = Mk1;
+  tg.kind = (Mk1 >= 1e-30 * (Mk + 2.0 * B) && Mk1 >= 1e-300) ? 0 : (is_zero(Mk1) ? 1 : 2);
+  tg.lnMk1 = tg.kind == 0 ? fsbm_log(Mk1, mt) : mt.ln_eps;
+  tg.sqMk1 = tg.kind == 0 ? sqrt(Mk1) : 0.0;
+  return tg;
+}
+// F for one pair (see TargetFP64). F >= 0 holds exactly (the factors' signs agree), so only
+// the upper clip is needed.
 __device__ __forceinline__ double bott_flux_fast(double dM, const TargetFP64& tg, double c, const MathTabs& mt) {
   const double g = tg.Mk + dM;
-  if (!tg.fast || __double_as_longlong(g) < 0x01a56e1fc2f8f359LL)  // g < 1e-300
+  if (__double_as_longlong(g) < 0x01a56e1fc2f8f359LL)  // g < 1e-300
     return bott_flux(dM, tg.Mk, tg.Mk1, c);
-  const double x1 = tg.lnMk1 - fsbm_log(g, mt);
+  const double rg = fsbm_rsqrt(g);
+  double x1, A;
+  if (tg.kind == 0) {
+    x1 = tg.lnMk1 - fsbm_log(g, mt);
+    A = tg.sqMk1 * rg;
+  } else if (tg.kind == 1) {
+    x1 = mt.ln_eps;
+    A = mt.sqrt_eps;
+  } else {
+    const double u = fma(kBottEps, g, tg.Mk1);
+    if (__double_as_longlong(u) < 0x01a56e1fc2f8f359LL) return bott_flux(dM, tg.Mk, tg.Mk1, c);
+    x1 = fsbm_log(u, mt) - fsbm_log(g, mt);
+    A = u * fsbm_rsqrt(u) * rg;
+  }
   if (is_zero(x1)) return min_nonneg(dM * c, dM);
-  const double A = tg.sqMk1 * fsbm_rsqrt(g);
   double E, em1;
   fsbm_exp_em1(-c * x1, mt, &E, &em1);
   return min_nonneg((dM * A) * (-em1) * fsbm_rcp(x1), dM);

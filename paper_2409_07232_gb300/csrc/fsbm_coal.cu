@@ -412,6 +412,8 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
     c->t.math.l64_hi = hi / 64.0;
     c->t.math.l64_lo = c->t.math.ln2_lo / 64.0;
     c->t.math.inv_l64 = (double)(64.0L / ln2);
+    c->t.math.ln_eps = std::log(kBottEps);
+    c->t.math.sqrt_eps = std::exp(0.5 * c->t.math.ln_eps);
   }
   std::stable_sort(cls.begin(), cls.end(), [](const Cls& a, const Cls& b) { return a.cost > b.cost; });
   std::memset(c->t.bucket_rank, -1, sizeof(c->t.bucket_rank));

@@ -32,6 +32,7 @@ struct MathTabs {
   double ln2_hi, ln2_lo;   // ln 2 = hi + lo
   double l64_hi, l64_lo;   // (ln 2) / 64 = hi + lo (the above divided by 64, exactly)
   double inv_l64;          // 64 / ln 2
+  double ln_eps, sqrt_eps; // ln(1e-60) and e^{ln(1e-60)/2}: Bott's constant in the flux
 };
 
 // ln x for normal x > 0 (callers guarantee x >= 1e-300). x = 2^e m with m in
