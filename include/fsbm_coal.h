@@ -149,6 +149,21 @@ FSBM_API fsbm_status fsbm_coal_step(fsbm_coal_ctx* ctx, const fsbm_coal_state* s
 FSBM_API fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* ctx, const fsbm_coal_state* host_state,
                                 int64_t n_points, double dt, int32_t n_steps);
 
+/* fsbm_coal_step without any device allocation. The paper has no counterpart: this is for
+ * callers that cannot let a library call cudaMalloc -- a host model that reserves all device
+ * memory in its own pool (for example several model processes sharing one GPU), or one that
+ * cannot take the device-wide synchronisation an allocation implies inside its time loop.
+ * Same arguments, same results and same stream semantics as fsbm_coal_step, but the
+ * compaction scratch lives in a fixed array inside the library (about 1.1 MB on every GPU
+ * that loads it, held until the process exits), so n_points is limited to 262144; larger
+ * batches return FSBM_E_ARG. The context's device must be current. The first call on a
+ * device looks the array up (cudaGetSymbolAddress): make it before any stream capture. All
+ * calls share the array, so calls that overlap on the GPU (different streams or threads) race
+ * and must be serialised by the caller. fsbm_coal_get_stats and fsbm_coal_get_active_list
+ * report fsbm_coal_step's own scratch, not this array. */
+FSBM_API fsbm_status fsbm_coal_step_noalloc(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points,
+                                            double dt, int32_t n_steps);
+
 /* Time the collision kernel for each candidate CTA size on a copy of (a sample of) the
  * given device state and keep the fastest for later steps. The caller's spectra are not
  * modified. Synchronous. */

@@ -35,7 +35,7 @@ _STATUS_NAMES = {0: "FSBM_OK", -1: "FSBM_E_ARG", -2: "FSBM_E_CUDA", -3: "FSBM_E_
                  -4: "FSBM_E_TIMEOUT", -5: "FSBM_E_UNSUPPORTED"}
 
 # Every entry point include/fsbm_coal.h declares.
-EXPORTS = ("fsbm_coal_init", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_autotune",
+EXPORTS = ("fsbm_coal_init", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_step_noalloc", "fsbm_coal_autotune",
            "fsbm_coal_set_graph", "fsbm_coal_set_block", "fsbm_coal_set_timing", "fsbm_coal_get_stats",
            "fsbm_coal_get_active_list", "fsbm_coal_math_check", "fsbm_coal_destroy", "fsbm_coal_last_error")
 
@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH):
             "fsbm_coal_step": ([V, P(fsbm_coal_state), ctypes.c_int64, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_step_host": ([V, P(fsbm_coal_state), ctypes.c_int64, ctypes.c_double, ctypes.c_int32],
                                     ctypes.c_int),
+            "fsbm_coal_step_noalloc": ([V, P(fsbm_coal_state), ctypes.c_int64, ctypes.c_double, ctypes.c_int32],
+                                       ctypes.c_int),
             "fsbm_coal_autotune": ([V, P(fsbm_coal_state), ctypes.c_int64], ctypes.c_int),
             "fsbm_coal_set_graph": ([V, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_set_block": ([V, ctypes.c_int32], ctypes.c_int),
@@ -183,6 +185,13 @@ def fsbm_coal_step(ctx, state: fsbm_coal_state, n_points: int, dt: float, n_step
 def fsbm_coal_step_host(ctx, state: fsbm_coal_state, n_points: int, dt: float, n_steps: int) -> None:
     _check(ctx, load().fsbm_coal_step_host(ctx, ctypes.byref(state), int(n_points), float(dt), int(n_steps)),
            "fsbm_coal_step_host")
+
+
+def fsbm_coal_step_noalloc(ctx, state: fsbm_coal_state, n_points: int, dt: float, n_steps: int) -> None:
+    """fsbm_coal_step with its scratch in a fixed array inside the library (no device
+    allocation; at most 262144 points per call)."""
+    _check(ctx, load().fsbm_coal_step_noalloc(ctx, ctypes.byref(state), int(n_points), float(dt), int(n_steps)),
+           "fsbm_coal_step_noalloc")
 
 
 def fsbm_coal_autotune(ctx, state: fsbm_coal_state, n_points: int) -> None:

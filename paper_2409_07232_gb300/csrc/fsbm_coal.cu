@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -670,3 +671,71 @@ fsbm_status fsbm_coal_math_check(fsbm_coal_ctx* c, double* out5) {
 const char* fsbm_coal_last_error(const fsbm_coal_ctx* c) { return c ? c->err.c_str() : kNullCtxMsg; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// fsbm_coal_step_noalloc: fsbm_coal_step for callers that must not allocate device memory.
+//
+// fsbm_coal_step sizes its scratch (the compaction pass's class counts, the list of active
+// points and two counters) with cudaMalloc the first time it sees a batch that large. Some
+// callers cannot let a library do that: a host model that reserves all device memory up
+// front in its own pool (several model processes sharing one GPU leave no headroom for a
+// library allocation), or one that cannot accept the device-wide synchronisation that
+// cudaMalloc and cudaFree imply in the middle of its time loop. This entry point runs the
+// same compaction pass and collision kernel with its scratch in a fixed array compiled into
+// the library, and calls no allocating routine.
+//
+// The array is sized for kNoAllocMaxPoints points (about 1.1 MB) and exists on every GPU that
+// loads the library until the process exits. The first call on a device looks up the array's
+// device address (cudaGetSymbolAddress) with that device current; make that first call
+// before any stream capture. All calls share the one array: two calls whose work overlaps on
+// the GPU (two streams or two host threads) race on it and must be ordered by the caller.
+// Every call rewrites all of the array it uses (the class counts, the list, and both
+// counters, which the scan kernel resets), so nothing left by a previous call is read.
+namespace {
+constexpr int64_t kNoAllocMaxPoints = 262144;
+constexpr int64_t kNoAllocMaxBlocks = (kNoAllocMaxPoints + kCompactThreads - 1) / kCompactThreads;
+constexpr int64_t kNoAllocWords = (int64_t)kNumBuckets * kNoAllocMaxBlocks + kNoAllocMaxPoints + 4;
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocWords];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int32_t* g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+extern "C" fsbm_status fsbm_coal_step_noalloc(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points,
+                                              double dt, int32_t n_steps) {
+  if (!c) return FSBM_E_ARG;
+  fsbm_status st = check_state(c, s, n_points, dt, n_steps);
+  if (st != FSBM_OK) return st;
+  if (n_points > kNoAllocMaxPoints)
+    return fail(c, FSBM_E_ARG,
+                "fsbm_coal_step_noalloc: n_points exceeds the fixed scratch capacity of 262144 points "
+                "(use fsbm_coal_step, or split the batch)");
+  int dev = -1;
+  CU(c, cudaGetDevice(&dev));
+  if (dev != c->device)
+    return fail(c, FSBM_E_ARG, "fsbm_coal_step_noalloc: the context's device must be the current device");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(c, FSBM_E_UNSUPPORTED, "fsbm_coal_step_noalloc: device ordinal");
+  int32_t* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(c, e, "fsbm_coal_step_noalloc: cudaGetSymbolAddress");
+      g_noalloc_addr[dev] = static_cast<int32_t*>(p);
+    }
+    base = g_noalloc_addr[dev];
+  }
+  st = ensure_plan(c);  // launch shape only (function attributes, occupancy): no allocation
+  if (st != FSBM_OK) return st;
+  Scratch sc{};
+  sc.n_blocks = (n_points + kCompactThreads - 1) / kCompactThreads;
+  sc.block_counts = base;
+  sc.active_list = base + (int64_t)kNumBuckets * kNoAllocMaxBlocks;
+  sc.counters = sc.active_list + kNoAllocMaxPoints;
+  const PointsDev p = to_dev(s);
+  CU(c, launch_compact(c->t, p, n_points, sc, c->stream));
+  CU(c, launch_coal(c->t, c->precision, p, sc, dt, n_steps, c->plan, c->stream));
+  return FSBM_OK;
+}
