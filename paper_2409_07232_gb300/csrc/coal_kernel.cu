@@ -91,51 +91,58 @@ __device__ __forceinline__ float bott_flux(float dM, float Mk, float Mk1, float 
   return fminf(fmaxf(F, 0.f), dM);
 }
 
-// FP32 flux, fast form. rho from the SFU reciprocal (2 ulp); ln rho = (e + log2 m) ln 2 with
-// m in [1/sqrt2, sqrt2), where the SFU's log2 has an absolute error near 2^-22.6, so ln rho
-// keeps an absolute error near 1e-7 at any magnitude; e^{x1/2} = sqrt(rho) through the SFU
-// reciprocal square root. (1 - e^{-z}) / x1 with z = c x1 is c times the series of
-// (1 - e^{-z}) / z for |z| <= 1 (twelve terms), and the direct form otherwise. rho = 0 (empty bin k+1) takes ln rho = ln 1e-60, e^{x1/2} = 1e-30 exactly
-// as the clamped FP32 reading does; subnormal or overflowing ratios use bott_flux above.
-__device__ __forceinline__ float bott_flux_f32(float dM, float Mk, float Mk1, float c) {
-  const float g = Mk + dM;
-  const float rho = __fdividef(Mk1, g);
+// FP32 flux, fast form, with the target bin's constants (M_k, M_{k+1}, and ln M_{k+1} when
+// M_{k+1} is below FP32's normal range) hoisted out of the pair loop.
+//  * rho = M_{k+1} / g from the SFU reciprocal (2 ulp), capped at 1e38;
+//  * rho normal: ln rho = (e + log2 m) ln 2 with m in [1/sqrt2, sqrt2), where the SFU's log2
+//    has an absolute error near 2^-22.6, so ln rho keeps an absolute error near 1e-7 at any
+//    magnitude; e^{x1/2} = sqrt(rho) through the SFU reciprocal square root;
+//  * rho below the normal range: ln rho = ln M_{k+1} - ln g, e^{x1/2} from the SFU
+//    exponential (relative error near 1e-6 there, where F is either negligible or clipped);
+//  * M_{k+1} = 0: ln rho = ln 1e-60 and e^{x1/2} = 1e-30, as the clamped FP32 reading does.
+// (1 - e^{-z}) / x1 with z = c x1 is c times the series of (1 - e^{-z}) / z for |z| <= 1
+// (twelve terms) and the direct form with the SFU exponential otherwise; both are evaluated
+// and one is selected, so the lanes of a warp do not diverge.
+struct TargetF32 {
+  float Mk, Mk1, lnMk1;
+  bool empty;
+};
+__device__ __forceinline__ float bott_flux_f32(float dM, const TargetF32& tg, float c) {
+  const float g = tg.Mk + dM;
+  const float rho = fminf(__fdividef(tg.Mk1, g), 1.0e38f);
   float x1, A;
-  if (rho >= 1.17549435e-38f && rho <= 3.0e38f) {
+  if (rho >= 1.17549435e-38f) {
     const int ix = __float_as_int(rho);
     const int e = (ix - 0x3f3504f3) >> 23;
     const float m = __int_as_float(ix - (e << 23));
     x1 = fmaf((float)e, 0.693147182f, __log2f(m) * 0.693147182f);
-    x1 = fminf(fmaxf(x1, kLnBottEps), 80.f);
     A = rho * rsqrtf(rho);
-  } else if (rho == 0.f) {
+  } else if (tg.empty) {
     x1 = kLnBottEps;
     A = 1.0e-30f;
   } else {
-    return bott_flux(dM, Mk, Mk1, c);
+    x1 = fmaxf(tg.lnMk1 - __logf(g), kLnBottEps);
+    A = __expf(0.5f * x1);
   }
+  x1 = fminf(x1, 80.f);
   const float z = c * x1;
-  float ratio;
-  if (fabsf(z) <= 1.f) {
-    // (1 - e^{-z}) / z = sum_k w^k / (k+1)!, w = -z, k = 0..11 (next term below 2e-10)
-    const float w = -z;
-    float q = fmaf(w, 1.f / 479001600.f, 1.f / 39916800.f);
-    q = fmaf(q, w, 1.f / 3628800.f);
-    q = fmaf(q, w, 1.f / 362880.f);
-    q = fmaf(q, w, 1.f / 40320.f);
-    q = fmaf(q, w, 1.f / 5040.f);
-    q = fmaf(q, w, 1.f / 720.f);
-    q = fmaf(q, w, 1.f / 120.f);
-    q = fmaf(q, w, 1.f / 24.f);
-    q = fmaf(q, w, 1.f / 6.f);
-    q = fmaf(q, w, 0.5f);
-    q = fmaf(q, w, 1.f);
-    ratio = c * q;
-  } else {
-    // |z| > 1: e^{-z} from the SFU exponential; 1 - e^{-z} then loses at most a factor
-    // e^{-1} / (1 - e^{-1}) < 0.6 of its relative accuracy
-    ratio = __fdividef(1.f - __expf(-z), x1);
-  }
+  // (1 - e^{-z}) / z = sum_k w^k / (k+1)!, w = -z, k = 0..11 (next term below 2e-10 at |z| = 1)
+  const float w = -z;
+  float q = fmaf(w, 1.f / 479001600.f, 1.f / 39916800.f);
+  q = fmaf(q, w, 1.f / 3628800.f);
+  q = fmaf(q, w, 1.f / 362880.f);
+  q = fmaf(q, w, 1.f / 40320.f);
+  q = fmaf(q, w, 1.f / 5040.f);
+  q = fmaf(q, w, 1.f / 720.f);
+  q = fmaf(q, w, 1.f / 120.f);
+  q = fmaf(q, w, 1.f / 24.f);
+  q = fmaf(q, w, 1.f / 6.f);
+  q = fmaf(q, w, 0.5f);
+  q = fmaf(q, w, 1.f);
+  // |z| > 1: 1 - e^{-z} loses at most a factor e^{-1} / (1 - e^{-1}) < 0.6 of the SFU
+  // exponential's accuracy; an overflowing e^{-z} gives ratio = +inf and F = dM (the clip)
+  const float direct = __fdividef(1.f - __expf(w), x1);
+  const float ratio = fabsf(z) <= 1.f ? c * q : direct;
   return fminf(dM * A * ratio, dM);
 }
 
@@ -229,11 +236,12 @@ struct Smem {
   T* N;           // [S][nmax]
   T* lam;         // [S][nmax]
   T* xs;          // [nmax]
+  T* cd;          // [nmax] Courant number per bin distance
   int* lim;       // [S*nmax] rows whose limiter ratio is below 1, ascending
   static __host__ __device__ size_t bytes(int nmax, int S) {
     size_t b = sizeof(double) * 2 * S * nmax + sizeof(Sum) * 2 * S * S * nmax;
     if (sizeof(T) != sizeof(double)) b += sizeof(T) * S * nmax;
-    b += sizeof(T) * (2 * S * nmax + nmax) + sizeof(int) * S * nmax;
+    b += sizeof(T) * (2 * S * nmax + 2 * nmax) + sizeof(int) * S * nmax;
     return (b + 15) & ~size_t(15);
   }
   __device__ void carve(unsigned char* base, int nmax, int S) {
@@ -257,6 +265,8 @@ struct Smem {
     lam = reinterpret_cast<T*>(p);
     p += sizeof(T) * S * nmax;
     xs = reinterpret_cast<T*>(p);
+    p += sizeof(T) * nmax;
+    cd = reinterpret_cast<T*>(p);
     p += sizeof(T) * nmax;
     lim = reinterpret_cast<int*>(p);
   }
@@ -348,70 +358,107 @@ template <> struct TargetOf<double> {
   }
 };
 template <> struct TargetOf<float> {
-  float Mk, Mk1;
+  TargetF32 tg;
   __device__ __forceinline__ void init(float mk, float mk1, double, const MathTabs&) {
-    Mk = mk;
-    Mk1 = mk1;
+    tg.Mk = mk;
+    tg.Mk1 = mk1;
+    tg.empty = is_zero(mk1);
+    tg.lnMk1 = (!tg.empty && mk1 < 1.17549435e-38f) ? logf(mk1) : 0.f;
   }
   __device__ __forceinline__ float flux(float dM, float c, const MathTabs&) const {
-    return bott_flux_f32(dM, Mk, Mk1, c);
+    return bott_flux_f32(dM, tg, c);
   }
 };
 
+// Gain pass for one (target bin k, orientation o) item per lane. A lane's pairs come in
+// groups (distance class kappa, larger bin m) whose distances d form one contiguous range; the
+// lane walks all its pairs in ONE loop, one pair per iteration, stepping d and moving to the
+// next non-empty group only when a range runs out. Lanes of a warp therefore stay in step
+// (no nested loops with per-lane trip counts), and the run counter for the FP32 sums is the
+// same in every lane.
+// Gain pass for one (target bin k, orientation o) item per lane. A lane's pairs come in
+// groups (distance class kappa, larger bin m) whose distances d form one contiguous range; the
+// lane walks all its pairs in ONE loop, one pair per iteration, stepping d and moving to the
+// next non-empty group only when a range runs out. Everything the loop reads more than once
+// (the orientation's fields, the group's constants) is copied into registers first: the
+// loop then touches shared memory only for the two spectrum values, the limiter ratio and
+// the Courant number of its pair.
 template <typename T, bool LIMITED>
-__device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T>& sm, const Orient& o,
+__device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T>& sm, const Orient& o_ref,
                                           const int* lo, const int* hi, int k, T dt, double B, const MathTabs& mt,
                                           typename Num<T>::Sum* out_stay, typename Num<T>::Sum* out_up) {
   const int n = G.n;
+  const Orient o = o_ref;  // register copy
+  const bool half = o.half != 0;
+  const int dmin = o.dmin;
+  const int kappa_max = G.kappa_max;
   Acc<T> stay, up;
-  if (k >= 1 && k < n) {
-    const T* __restrict__ Kd = Sel<T>::Kd(G) + o.table;
-    const T* __restrict__ cd = Sel<T>::cd(G);
-    const T* Ns = sm.N + o.s * n;
-    const T* Nl = sm.N + o.l * n;
-    const T* Ms = sm.Mt + o.s * n;
-    const T* Ls = sm.lam + o.s * n;
-    const T* Ll = sm.lam + o.l * n;
-    const int lo_s = lo[o.s], hi_s = hi[o.s], lo_l = lo[o.l], hi_l = hi[o.l];
-    const bool top = (k == n - 1);
-    // regular target: pairs with m + kappa[d] == k; top bin: every pair with m + kappa[d] >= n-1
-    // stays there without a flux
-    TargetOf<T> tgt;
-    tgt.init(top ? T(0) : sm.Mt[o.c * n + k], top ? T(0) : sm.Mt[o.c * n + k + 1], B, mt);
-    for (int kap = 0; kap <= G.kappa_max; ++kap) {
-      const int mlo = top ? max(n - 1 - kap, lo_l) : max(k - kap, lo_l);
-      const int mhi = top ? min(n - 1, hi_l) : min(k - kap, hi_l);
-      for (int m = mlo; m <= mhi; ++m) {
-        const int d0 = max(max(G.d_lo[kap], (int)o.dmin), m - hi_s);
-        const int d1 = min(G.d_hi[kap], m - lo_s);
-        const T nl = Nl[m] * dt;
-        const T xl = sm.xs[m];
-        const T ll = LIMITED ? Ll[m] : T(1);
-        // one pair (m - d, m): dM = C (x_i + x_m) = K N_m dt (M_i + N_i x_m) h phi
-        auto pair = [&](int d, T h) {
-          const int i = m - d;
-          T dM = __ldg(Kd + ((size_t)d * n + m) * S2) * nl * fma(Ns[i], xl, Ms[i]) * h;
-          if (LIMITED) dM *= (Ls[i] < ll ? Ls[i] : ll);
-          if (pos(dM)) {
-            const T c = __ldg(cd + d);
-            stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
-            if (!top && !is_zero(c)) up.add(tgt.flux(dM, c, mt));  // none out of the top bin; c = 0: F = 0
-          }
-        };
-        int dstart = d0;
-        if (o.half && d0 == 0 && d1 >= 0) {  // the same-species diagonal pair counts once: h = 1/2
-          pair(0, T(0.5));
-          dstart = 1;
-        }
-        for (int r0 = dstart; r0 <= d1; r0 += kGainRun) {
-          const int r1 = min(d1, r0 + kGainRun - 1);
-          for (int d = r0; d <= r1; ++d) pair(d, T(1));
-          stay.flush();
-          up.flush();
-        }
+  const T* __restrict__ Kd = Sel<T>::Kd(G) + o.table;
+  const T* __restrict__ Ns = sm.N + o.s * n;
+  const T* __restrict__ Nl = sm.N + o.l * n;
+  const T* __restrict__ Ms = sm.Mt + o.s * n;
+  const T* __restrict__ Ls = sm.lam + o.s * n;
+  const T* __restrict__ Ll = sm.lam + o.l * n;
+  const T* __restrict__ xs = sm.xs;
+  const T* __restrict__ cds = sm.cd;
+  const int lo_s = lo[o.s], hi_s = hi[o.s], lo_l = lo[o.l], hi_l = hi[o.l];
+  const bool valid = k >= 1 && k < n;
+  const bool top = k == n - 1;
+  // regular target: pairs with m + kappa(d) == k; top bin: every pair with m + kappa(d) >= n-1
+  // stays there without a flux
+  TargetOf<T> tgt;
+  tgt.init(valid && !top ? sm.Mt[o.c * n + k] : T(0), valid && !top ? sm.Mt[o.c * n + k + 1] : T(0), B, mt);
+  const int kstride = n * S2;
+  int kap = -1, m = 1, mhi = 0, d = 0, d1 = -1, ko = 0;
+  T nl = T(0), xl = T(0), ll = T(1);
+  auto next_group = [&]() -> bool {
+    for (;;) {
+      if (m > mhi) {
+        if (++kap > kappa_max) return false;
+        m = top ? max(n - 1 - kap, lo_l) : max(k - kap, lo_l);
+        mhi = top ? min(n - 1, hi_l) : min(k - kap, hi_l);
+        continue;
       }
+      d = max(max(G.d_lo[kap], dmin), m - hi_s);
+      d1 = min(G.d_hi[kap], m - lo_s);
+      if (d <= d1) {
+        nl = Nl[m] * dt;
+        xl = xs[m];
+        if (LIMITED) ll = Ll[m];
+        ko = (d * n + m) * S2;
+        return true;
+      }
+      ++m;
+    }
+  };
+  bool live = valid && next_group();
+  int cnt = 0;
+  while (live) {
+    // one pair (m - d, m): dM = C (x_i + x_m) = K N_m dt (M_i + N_i x_m) h phi, h = 1/2 for
+    // the same-species diagonal pair (counted once)
+    const int i = m - d;
+    T dM = __ldg(Kd + ko) * nl * fma(Ns[i], xl, Ms[i]);
+    if (half && d == 0) dM *= T(0.5);
+    if (LIMITED) dM *= fmin(Ls[i], ll);
+    if (pos(dM)) {
+      const T c = cds[d];
+      stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
+      if (!top && !is_zero(c)) up.add(tgt.flux(dM, c, mt));  // none out of the top bin; c = 0: F = 0
+    }
+    ++d;
+    ko += kstride;
+    if (d > d1) {
+      ++m;
+      live = next_group();
+    }
+    if (++cnt == kGainRun) {
+      stay.flush();
+      up.flush();
+      cnt = 0;
     }
   }
+  stay.flush();
+  up.flush();
   typename Num<T>::Sum st = stay.sum(), u = up.sum();
   Num<T>::sub(st, u);
   *out_stay = st;
@@ -468,7 +515,10 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
       bad |= !(v >= 0.0) || !(v <= DBL_MAX);
       sm.M[e] = v;
     }
-    for (int k = tid; k < n; k += NT) sm.xs[k] = Sel<T>::x(G)[k];
+    for (int k = tid; k < n; k += NT) {
+      sm.xs[k] = Sel<T>::x(G)[k];
+      sm.cd[k] = Sel<T>::cd(G)[k];
+    }
     if (__syncthreads_or(bad)) {
       if (tid == 0) {
         pd.status[p] = 2;
