@@ -54,11 +54,11 @@ FP64_PER_CLK = 2            # FP64 operations per clock per SM (the probe measur
 #             (1 - e^-z)/z series 12, F and clip 3, mat-vec 2 = 32 FMA-pipe operations,
 #             and 4 SFU operations (reciprocal, log2, reciprocal square root, and one more
 #             in the exponential branch);
-#  FP64 form: dM 3, sums 2, g 1, ln 13, x1 1, e^{x1/2} 6, z 1, e^y - 1 17, F 6,
-#             mat-vec 2 = 52 FP64-pipe operations.
+#  FP64 form: dM 3, sums 2, g 1, ln 10, x1 1, e^{x1/2} 6, z 1, e^y - 1 11, F 6,
+#             mat-vec 2 = 43 FP64-pipe operations.
 FP_OPS_PER_PAIR = 32
 MUFU_OPS_PER_PAIR = 4
-FP64_OPS_PER_PAIR = 52
+FP64_OPS_PER_PAIR = 43
 
 
 def pairs_per_point(n, ns):

@@ -34,7 +34,6 @@ struct Orient {
   int8_t s, l;      // slots of the small-index and the large-index partner
   int8_t dmin;      // 0, or 1 when the two species' roles are swapped (d = 0 belongs to the
                     // other orientation of the same species pair)
-  int8_t half;      // same species: the diagonal pair counts once, h = 1/2
   int8_t c;         // slot of the product species
   int table;        // s_id * S + l_id: position of the orientation inside a Kd row
 };
@@ -77,20 +76,7 @@ __device__ __forceinline__ double bott_flux(double dM, double Mk, double Mk1, do
 // FP32 form. 1e-60 is below FP32's range, so ln(rho + 1e-60) becomes ln(rho) clamped at
 // ln(1e-60); the two differ only for rho within a few orders of 1e-60. ln(rho) is capped at
 // 80, above which F >= dM for every c > 0 (and F = 0 for c = 0) in either form.
-__device__ __forceinline__ float bott_flux(float dM, float Mk, float Mk1, float c) {
-  const float g = Mk + dM;
-  float x1 = logf(Mk1 / g);
-  x1 = fminf(fmaxf(x1, kLnBottEps), 80.f);
-  float F;
-  if (x1 == 0.f) {
-    F = dM * c;
-  } else {
-    const float z = -c * x1;
-    F = (z > 80.f) ? dM : dM * expf(0.5f * x1) * (-expm1f(z)) / x1;
-  }
-  return fminf(fmaxf(F, 0.f), dM);
-}
-
+//
 // FP32 flux, fast form, with the target bin's constants (M_k, M_{k+1}, and ln M_{k+1} when
 // M_{k+1} is below FP32's normal range) hoisted out of the pair loop.
 //  * rho = M_{k+1} / g from the SFU reciprocal (2 ulp), capped at 1e38;
@@ -298,6 +284,7 @@ __device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) << 
 __device__ __forceinline__ double min_nonneg(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b) ? a : b;
 }
+__device__ __forceinline__ float min_nonneg(float a, float b) { return fminf(a, b); }
 // Bott's flux with target-bin constants hoisted out of the pair loop:
 //  * bin k+1 holds at least 1e-30 of the largest content bin k can reach (Mk + 2B): then
 //    ln(rho + 1e-60) = ln M_{k+1} - ln g to 1e-30 and e^{x1/2} = sqrt(M_{k+1}) / sqrt(g);
@@ -373,12 +360,6 @@ template <> struct TargetOf<float> {
 // Gain pass for one (target bin k, orientation o) item per lane. A lane's pairs come in
 // groups (distance class kappa, larger bin m) whose distances d form one contiguous range; the
 // lane walks all its pairs in ONE loop, one pair per iteration, stepping d and moving to the
-// next non-empty group only when a range runs out. Lanes of a warp therefore stay in step
-// (no nested loops with per-lane trip counts), and the run counter for the FP32 sums is the
-// same in every lane.
-// Gain pass for one (target bin k, orientation o) item per lane. A lane's pairs come in
-// groups (distance class kappa, larger bin m) whose distances d form one contiguous range; the
-// lane walks all its pairs in ONE loop, one pair per iteration, stepping d and moving to the
 // next non-empty group only when a range runs out. Everything the loop reads more than once
 // (the orientation's fields, the group's constants) is copied into registers first: the
 // loop then touches shared memory only for the two spectrum values, the limiter ratio and
@@ -389,7 +370,6 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
                                           typename Num<T>::Sum* out_stay, typename Num<T>::Sum* out_up) {
   const int n = G.n;
   const Orient o = o_ref;  // register copy
-  const bool half = o.half != 0;
   const int dmin = o.dmin;
   const int kappa_max = G.kappa_max;
   Acc<T> stay, up;
@@ -434,12 +414,11 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
   bool live = valid && next_group();
   int cnt = 0;
   while (live) {
-    // one pair (m - d, m): dM = C (x_i + x_m) = K N_m dt (M_i + N_i x_m) h phi, h = 1/2 for
-    // the same-species diagonal pair (counted once)
+    // one pair (m - d, m): dM = C (x_i + x_m) = K N_m dt (M_i + N_i x_m) h phi; the table
+    // entry of the same-species diagonal pair already holds h K = K / 2
     const int i = m - d;
     T dM = __ldg(Kd + ko) * nl * fma(Ns[i], xl, Ms[i]);
-    if (half && d == 0) dM *= T(0.5);
-    if (LIMITED) dM *= fmin(Ls[i], ll);
+    if (LIMITED) dM *= min_nonneg(Ls[i], ll);
     if (pos(dM)) {
       const T c = cds[d];
       stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
@@ -553,8 +532,8 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
           const int ia = s_sp[a], ib = s_sp[b];
           const int prod = t.product[ia * S + ib];
           const int cs = (prod == ia) ? a : b;
-          ori[q++] = Orient{(int8_t)a, (int8_t)b, 0, (int8_t)(a == b), (int8_t)cs, ia * S + ib};
-          if (a != b) ori[q++] = Orient{(int8_t)b, (int8_t)a, 1, 0, (int8_t)cs, ib * S + ia};
+          ori[q++] = Orient{(int8_t)a, (int8_t)b, 0, (int8_t)cs, ia * S + ib};
+          if (a != b) ori[q++] = Orient{(int8_t)b, (int8_t)a, 1, (int8_t)cs, ib * S + ia};
         }
     }
     __syncthreads();

@@ -358,10 +358,13 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
     for (int s = 0; s < S; ++s)
       for (int l = 0; l < S; ++l) {
         double* kr = Kr.data() + (size_t)(s * S + l) * nn;
-        // Kd[d][m][s*S+l]: the orientations of one (d, m) sit side by side
+        // Kd[d][m][s*S+l]: the orientations of one (d, m) sit side by side. The same-species
+        // diagonal pair (d = 0, s = l) is counted once with weight 1/2 (Sec. II's collection
+        // of a bin with itself), so its entry holds K / 2 and the gain pass needs no weight.
         for (int d = 0; d < n; ++d)
           for (int m = d; m < n; ++m)
-            Kd[((size_t)d * n + m) * S2 + (s * S + l)] = kern_entry(Kg, S, n, s, m - d, l, m);
+            Kd[((size_t)d * n + m) * S2 + (s * S + l)] =
+                kern_entry(Kg, S, n, s, m - d, l, m) * ((d == 0 && s == l) ? 0.5 : 1.0);
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) kr[(size_t)j * n + i] = kern_entry(Kg, S, n, s, i, l, j);
       }
@@ -388,19 +391,22 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
   {
     // tables of the FP64 logarithm and exponential (Tang's table-driven methods), in long double
     std::vector<double> lt(2 * kLogTab), et(2 * kExpTab);
-    for (int t = 0; t < kLogTab; ++t) {
-      const long double F = 1.0L + (long double)(t + kLogTabLo) / 256.0L;
-      lt[2 * t] = (double)(1.0L / F);
-      lt[2 * t + 1] = (double)logl(F);
+    for (int j = 0; j < kLogTab; ++j) {
+      const long double F = 1.0L + (long double)j / 512.0L;
+      lt[2 * j] = (double)(1.0L / F);
+      lt[2 * j + 1] = (double)logl(F);
     }
     for (int j = 0; j < kExpTab; ++j) {
-      const long double v = exp2l((long double)j / 64.0L);
+      const long double v = exp2l((long double)j / 256.0L);
       et[2 * j] = (double)v;
       et[2 * j + 1] = (double)(v - (long double)et[2 * j]);
     }
     fsbm_status st;
-    if ((st = upload(c, lt, &c->t.math.logtab)) != FSBM_OK || (st = upload(c, et, &c->t.math.exptab)) != FSBM_OK)
-      return bail(st);
+    const double* ltd = nullptr;
+    const double* etd = nullptr;
+    if ((st = upload(c, lt, &ltd)) != FSBM_OK || (st = upload(c, et, &etd)) != FSBM_OK) return bail(st);
+    c->t.math.logtab = reinterpret_cast<const double2*>(ltd);  // cudaMalloc: 256-byte aligned
+    c->t.math.exptab = reinterpret_cast<const double2*>(etd);
     const long double ln2 = logl(2.0L);
     uint64_t bits;
     const double ln2d = (double)ln2;
@@ -410,9 +416,9 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
     std::memcpy(&hi, &bits, sizeof hi);
     c->t.math.ln2_hi = hi;
     c->t.math.ln2_lo = (double)(ln2 - (long double)hi);
-    c->t.math.l64_hi = hi / 64.0;
-    c->t.math.l64_lo = c->t.math.ln2_lo / 64.0;
-    c->t.math.inv_l64 = (double)(64.0L / ln2);
+    c->t.math.l256_hi = hi / 256.0;
+    c->t.math.l256_lo = c->t.math.ln2_lo / 256.0;
+    c->t.math.inv_l256 = (double)(256.0L / ln2);
     c->t.math.ln_eps = std::log(kBottEps);
     c->t.math.sqrt_eps = std::exp(0.5 * c->t.math.ln_eps);
   }

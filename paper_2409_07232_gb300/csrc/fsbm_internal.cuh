@@ -7,7 +7,8 @@
 //                     with c = ((1 + alpha^-d) alpha^-kappa - 1) / (alpha - 1), so both
 //                     depend on d only (the pair tables of Sec. V-A shrink to length n).
 //   x[k]              bin masses.
-//   Kd[d][m][s*S+l]   kernel of species s bin m-d with species l bin m, the S*S ordered
+//   Kd[d][m][s*S+l]   kernel of species s bin m-d with species l bin m (halved for the
+//                     same-species diagonal d = 0, s = l, which counts once), the S*S ordered
 //                     species pairs innermost: the gain pass puts one lane per species
 //                     orientation on the same (d, m), so a warp's loads are contiguous.
 //   Kr[a][b][j][i]    kernel of species a bin i with species b bin j (i fastest): the

@@ -1,97 +1,94 @@
 // fsbm_math.cuh -- table-driven FP64 logarithm and exponential for the FP64 pair flux.
 //
 // GB300 runs FP64 at about 1/64 of its FP32 rate, so the FP64 form of the collision kernel is
-// bound by FP64 instructions per bin pair, most of which go to the logarithm and the two
-// exponentials of Bott's flux. These routines follow P. T. P. Tang's table-driven methods
+// bound by FP64 instructions per bin pair, most of which go to the logarithm and the
+// exponential of Bott's flux. These routines follow P. T. P. Tang's table-driven methods
 // ("Table-driven implementation of the exponential function in IEEE floating-point
 // arithmetic", ACM TOMS 15(2), 1989; "... the logarithm function ...", ACM TOMS 16(4),
 // 1990; "... the expm1 function ...", ACM TOMS 18(2), 1992): a table reduces the argument to
 // a short interval, a low-degree Taylor polynomial finishes it, and integer operations
-// handle the binary exponent. The polynomial degrees are cut to what the flux needs (its
-// result must agree to 1e-12): about 1e-16 absolute for ln, 1e-15 relative for e^y and
-// e^y - 1, checked against CUDA's log/exp/expm1 by fsbm_coal_math_check.
+// handle the binary exponent, the table index and the reduced argument's table point (the
+// integer pipes are idle in this kernel, the FP64 pipe is not). The tables are large enough
+// that degree-4 polynomials reach what the flux needs (its result must agree to 1e-12):
+// about 2e-16 absolute for ln (the flux only uses differences of logarithms), 4e-16 relative
+// for e^y and 3e-14 relative for e^y - 1 (near y = 0, where the series' r^4/120 decides),
+// checked against CUDA's log/exp/expm1 by fsbm_coal_math_check.
 //
-// Tables (built on the host in FP64, copied to the device once per context):
-//   logtab[2*(j+75)], logtab[2*(j+75)+1] = 1 / F_j, ln F_j for F_j = 1 + j/256, j = -75..106
-//                                           (F covers [1/sqrt2, sqrt2], the reduced mantissa)
-//   exptab[2*j], exptab[2*j+1]  = 2^(j/64) = hi + lo (lo: the rounding error of hi)
+// Tables (built on the host in extended precision, rounded to FP64, copied to the device once
+// per context), both read as one 16-byte load per call:
+//   logtab[j] = (1 / F_j, ln F_j) for F_j = 1 + j/512, j = 0..512
+//   exptab[j] = (hi, lo) with hi + lo = 2^(j/256), j = 0..255 (lo: the rounding error of hi)
 #pragma once
 #include <cstdint>
+#include <cuda_runtime.h>
 
 namespace fsbm {
 
-constexpr int kLogTabLo = -75;
-constexpr int kLogTab = 182;
-constexpr int kExpTab = 64;
+constexpr int kLogTab = 513;
+constexpr int kExpTab = 256;
 
-// The constants: ln 2 = hi + lo with the 32 low mantissa bits of hi cleared, so that e * hi is
-// exact for |e| < 2^11 and N * hi / 64 for |N| < 2^17; and 64 / ln 2. Built on the host.
+// ln 2 = hi + lo with the 32 low mantissa bits of hi cleared, so that e * hi is exact for
+// |e| < 2^11 and N * hi / 256 for |N| < 2^20; and 256 / ln 2. Built on the host.
 struct MathTabs {
-  const double* logtab;   // [2 * kLogTab]
-  const double* exptab;   // [2 * kExpTab]
+  const double2* logtab;   // [kLogTab]
+  const double2* exptab;   // [kExpTab]
   double ln2_hi, ln2_lo;   // ln 2 = hi + lo
-  double l64_hi, l64_lo;   // (ln 2) / 64 = hi + lo (the above divided by 64, exactly)
-  double inv_l64;          // 64 / ln 2
+  double l256_hi, l256_lo; // (ln 2) / 256 = hi + lo (the above divided by 256, exactly)
+  double inv_l256;         // 256 / ln 2
   double ln_eps, sqrt_eps; // ln(1e-60) and e^{ln(1e-60)/2}: Bott's constant in the flux
 };
 
-// ln x for normal x > 0 (callers guarantee x >= 1e-300). x = 2^e m with m in
-// [1/sqrt2, sqrt2), so e = 0 near x = 1 and no table rounding is left to cancel there.
+// ln x for normal x > 0 (callers guarantee x >= 1e-300), absolute error about 2e-16 plus the
+// rounding of the result. x = 2^e m with m in [1, 2); F = 1 + j/512 is the table point
+// nearest m, built from the index bits (so m - F is exact, |m - F| <= 2^-10) and
+// ln x = e ln2 + ln F + ln(1 + u) with u = (m - F) / F, |u| <= 2^-10.
 __device__ __forceinline__ double fsbm_log(double x, const MathTabs& mt) {
-  const double* __restrict__ logtab = mt.logtab;
   const int hi = __double2hiint(x);
   const int lo = __double2loint(x);
-  int e = (hi >> 20) - 1023;
+  const int e = (hi >> 20) - 1023;
   const int mb = hi & 0x000fffff;
-  int j;
-  double m;
-  if (mb >= 0x6a09e) {                              // mantissa >= sqrt2: halve it
-    e += 1;
-    m = __hiloint2double(mb | 0x3fe00000, lo);      // in [1/sqrt2, 1)
-    j = ((mb - 0x100000) + 0x1000) >> 13;           // nearest (m - 1) * 256, in [-75, 0]
-  } else {
-    m = __hiloint2double(mb | 0x3ff00000, lo);      // in [1, sqrt2)
-    j = (mb + 0x800) >> 12;                         // nearest (m - 1) * 256, in [0, 106]
-  }
-  const double F = fma((double)j, 1.0 / 256.0, 1.0);
-  const double f = m - F;                           // exact: |f| <= 1/512
-  const int t = 2 * (j - kLogTabLo);
-  const double u = f * __ldg(logtab + t);           // f / F, |u| <= 2^-8.5
-  // ln(1 + u) = u - u^2/2 + u^3/3 - u^4/4 + u^5/5; the next term is below 2^-51 / 6 = 7e-17
-  // (absolute), which is the accuracy the flux needs: it uses differences of logarithms.
-  double q = fma(u, 1.0 / 5.0, -0.25);
-  q = fma(q, u, 1.0 / 3.0);
+  const int j = (mb + 0x400) >> 11;                         // nearest j / 512, in [0, 512]
+  const double m = __hiloint2double(mb | 0x3ff00000, lo);   // in [1, 2)
+  const double F = __hiloint2double(0x3ff00000 + (j << 11), 0);
+  const double2 t = __ldg(mt.logtab + j);
+  const double u = (m - F) * t.x;
+  // ln(1 + u) = u - u^2/2 + u^3/3 - u^4/4; the next term is below 2^-50 / 5 = 1.8e-16
+  double q = fma(u, -0.25, 1.0 / 3.0);
   q = fma(q, u, -0.5);
   const double lp = fma(u * u, q, u);
   const double de = (double)e;
-  return fma(de, mt.ln2_hi, __ldg(logtab + t + 1)) + fma(de, mt.ln2_lo, lp);
+  return fma(de, mt.ln2_hi, t.y) + fma(de, mt.ln2_lo, lp);
 }
 
 // e^y (*ex) and e^y - 1 (*em1) for |y| <= 700, from one reduction:
-// y = (64 M + j) ln2/64 + r, |r| <= ln2/128, e^y = 2^M 2^(j/64) (1 + p(r)).
-// e^y - 1 = (s - 1) + s p with s = 2^M 2^(j/64); s - 1 is exact whenever the result is
+// y = (256 M + j) ln2/256 + r, |r| <= ln2/512, e^y = 2^M 2^(j/256) (1 + p(r)).
+// e^y - 1 = (s - 1) + s p with s = 2^M 2^(j/256); s - 1 is exact whenever the result is
 // small (M = 0, j = 0 near y = 0), which is what keeps e^y - 1 accurate there.
 __device__ __forceinline__ void fsbm_exp_em1(double y, const MathTabs& mt, double* ex, double* em1) {
-  const double* __restrict__ exptab = mt.exptab;
-  const double t = y * mt.inv_l64;
-  const double Nd = rint(t);
-  const int N = (int)Nd;
-  double r = fma(-Nd, mt.l64_hi, y);
-  r = fma(-Nd, mt.l64_lo, r);
-  // e^r - 1 = r + r^2/2 + r^3/6 + r^4/24 + r^5/120; the next term is below 7e-15 of the
-  // result (|r| <= ln2/128), the relative accuracy the flux needs for e^y - 1 near y = 0
-  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  p = fma(p, r, 1.0 / 6.0);
+  // N = nearest integer to 256 y / ln2: adding 1.5 * 2^52 rounds it into the low word
+  constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52
+  const double kd = fma(y, mt.inv_l256, kShift);
+  const int N = __double2loint(kd);
+  const double Nd = kd - kShift;
+  double r = fma(-Nd, mt.l256_hi, y);
+  r = fma(-Nd, mt.l256_lo, r);
+  // e^r - 1 = r + r^2/2 + r^3/6 + r^4/24; the next term is r^4/120 <= 2.8e-14 of the
+  // result (|r| <= ln2/512), which bounds e^y - 1's relative error near y = 0
+  double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   p = fma(p, r, 0.5);
   p = fma(r * r, p, r);
-  const int jj = N & 63;
-  const int M = N >> 6;                            // floor division
-  // s = 2^M * 2^(jj/64) = s_hi + s_lo: add M to the exponent field of both table parts
-  const double th = __ldg(exptab + 2 * jj), tl = __ldg(exptab + 2 * jj + 1);
+  const int jj = N & 255;
+  const int M = N >> 8;                            // floor division
+  // s = 2^M * 2^(jj/256) = s_hi + s_lo: add M to the exponent field of both table parts.
+  // lo is 0 at jj = 0; where lo 2^M would leave the normal range it is below 2^-1022 and
+  // is dropped.
+  const double2 t = __ldg(mt.exptab + jj);
   const int sh = (int)((unsigned)M << 20);
-  const double s_hi = __hiloint2double(__double2hiint(th) + sh, __double2loint(th));
-  const double s_lo = tl * __hiloint2double((M + 1023) << 20, 0);  // tl 2^M (tl is tiny: scale by multiply)
-  const double tail = fma(s_hi, p, s_lo * (1.0 + p));  // s p + s_lo, the small part
+  const double s_hi = __hiloint2double(__double2hiint(t.x) + sh, __double2loint(t.x));
+  const int lh = __double2hiint(t.y);
+  const int le = (lh >> 20) & 0x7ff;
+  const double s_lo = (le != 0 && le + M > 0) ? __hiloint2double(lh + sh, __double2loint(t.y)) : 0.0;
+  const double tail = fma(s_hi, p, s_lo);          // s p + s_lo (s_lo p is below 2^-60 s)
   *ex = s_hi + tail;
   *em1 = (s_hi - 1.0) + tail;                      // s_hi - 1 is exact when the result is small
 }
