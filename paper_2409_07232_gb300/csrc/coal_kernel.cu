@@ -22,6 +22,7 @@
 //      are added in a fixed order: the result does not depend on scheduling;
 //   5. M' = M - loss + gain (FP64), mass error, round-off negatives to 0, rescale to B.
 // FP32_SPLIT runs 2-4 with float values and float sums; 1 and 5 stay FP64.
+#include <algorithm>
 #include <cfloat>
 #include <cstdio>
 
@@ -735,6 +736,22 @@ cudaError_t plan_t(const Tables& t, int block_dim, int n_sms, CoalLaunch* out) {
   const size_t smem = Smem<T>::bytes(nmax, t.S);
   cudaError_t e = cudaFuncSetAttribute(k_coal<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // Give shared memory what the register-limited number of resident CTAs needs and leave the
+  // rest of the SM's 256 KB to L1 (the kernel and math tables are read through it).
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, k_coal<T>);
+  if (e != cudaSuccess) return e;
+  int dev = 0, regs_sm = 0, smem_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  const int regs_cta = ((fa.numRegs * 32 + 255) / 256 * 256) * (block_dim / 32);  // per-warp allocation unit 256
+  const int by_regs = std::max(regs_cta > 0 ? regs_sm / regs_cta : 1, 1);
+  const size_t need = (size_t)by_regs * (smem + fa.sharedSizeBytes + 1024);
+  const int carve = (int)std::min<size_t>(100, (need * 100 + smem_sm - 1) / std::max(smem_sm, 1));
+  if ((e = cudaFuncSetAttribute(k_coal<T>, cudaFuncAttributePreferredSharedMemoryCarveout, carve)) != cudaSuccess)
+    return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coal<T>, block_dim, smem);
   if (e != cudaSuccess) return e;
