@@ -27,6 +27,7 @@ independent, so there is no collective in the data path.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -59,6 +60,39 @@ FP64_PER_CLK = 2            # FP64 operations per clock per SM (the probe measur
 FP_OPS_PER_PAIR = 32
 MUFU_OPS_PER_PAIR = 4
 FP64_OPS_PER_PAIR = 43
+
+
+L2_BYTES = 129e6
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of k_coal<double>, from one ncu
+# capture of a launch over a 100,000-point sample of the CONUS-shaped domain (inputs larger than
+# L2), per active point; a full-domain launch is that times its active points. It holds only for
+# the kernel sources it was taken on: after any change to them the bench reports null.
+DRAM_TRAFFIC = {"kernel": "k_coal<double>", "bytes_per_active_point": 2331.17,
+                "sources_sha256": "63f04b04301f6d8c8699e852d04a3455003b61f4a3cc6bd37acefe8355ff37ee",
+                "profile": "profiles/k_coal_fp64_conus100k_dram.md"}
+KERNEL_SOURCES = ("paper_2409_07232_gb300/csrc/coal_kernel.cu", "paper_2409_07232_gb300/csrc/fsbm_math.cuh",
+                  "paper_2409_07232_gb300/csrc/fsbm_internal.cuh")
+
+
+def kernel_traffic(precision, n_active):
+    """DRAM bytes of one collision launch from the recorded capture, or None if it does not apply."""
+    if precision != 0:
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != DRAM_TRAFFIC["sources_sha256"]:
+        return None
+    return DRAM_TRAFFIC["bytes_per_active_point"] * n_active
+
+
+def l2_note(spectra_bytes):
+    if spectra_bytes > L2_BYTES:
+        return "inputs larger than L2 (spectra %.2f GB)" % (spectra_bytes / 1e9)
+    return ("inputs smaller than L2 (spectra %.3f GB), no flush between steps: a profiling or test "
+            "size, not the bench configuration" % (spectra_bytes / 1e9))
 
 
 def pairs_per_point(n, ns):
@@ -342,7 +376,7 @@ def main():
             "active_points": n_active,
             "collision_steps_per_call": w.n_steps,
             "bin_pairs_per_call": n_pairs * w.n_steps,
-            "l2": "inputs larger than L2 (spectra %.2f GB)" % (w.spectra.size * (8 if precision == 0 else 4) / 1e9),
+            "l2": l2_note(w.spectra.size * (8 if precision == 0 else 4)),
             "parallelism": f"dp{world} (independent points, weak scaling)",
         },
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
@@ -351,7 +385,7 @@ def main():
         "gpu_launches": 4 * args.steps,
         "block_dim": st["block_dim"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": kernel_traffic(precision, n_active),
                      "kernel": "k_coal<%s>" % ("double" if precision == 0 else "float"),
                      "peak_basis": "FP64 pipe %d/clk/SM / %d FP64 ops per pair" % (FP64_PER_CLK, FP64_OPS_PER_PAIR)
                      if precision == 0 else "min(FP32 %d/clk/SM / %d ops, MUFU %d/clk/SM / %d ops) per pair" % (

@@ -164,9 +164,11 @@ FSBM_API fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* ctx, const fsbm_coal_sta
 FSBM_API fsbm_status fsbm_coal_step_noalloc(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points,
                                             double dt, int32_t n_steps);
 
-/* Time the collision kernel for each candidate CTA size on a copy of (a sample of) the
- * given device state and keep the fastest for later steps. The caller's spectra are not
- * modified. Synchronous. */
+/* Time the collision kernel for each candidate CTA size (128, 256, 512 threads) on a copy of
+ * the first 2^18 points of the given device state (all of it if smaller), three collision
+ * steps of 5 s each, and keep the fastest for later steps. The caller's spectra are not
+ * modified. Synchronous; allocates a temporary copy of the sample. The paper has no
+ * counterpart. */
 FSBM_API fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points);
 
 /* Enable (1) or disable (0, the default) CUDA-graph capture of fsbm_coal_step: the first

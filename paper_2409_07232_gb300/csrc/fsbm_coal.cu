@@ -515,7 +515,10 @@ fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64
   fsbm_status st = check_state(c, s, n_points, 1.0, 1);
   if (st != FSBM_OK) return st;
   if (n_points == 0) return FSBM_OK;
-  const int64_t P = std::min<int64_t>(n_points, 1 << 17);
+  // A sample of up to 2^18 points runs 3 collision steps per candidate: long enough that the
+  // per-point start-up work and the last points' tail weigh about as much as in a real call.
+  const int64_t P = std::min<int64_t>(n_points, 1 << 18);
+  constexpr int kTuneSteps = 3;
   int64_t off[2];
   CU(c, cudaMemcpyAsync(&off[0], s->offset, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaMemcpyAsync(&off[1], s->offset + P, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
@@ -551,7 +554,7 @@ fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64
       cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
       launch_compact(c->t, p, P, c->scratch, c->stream);
       cudaEventRecord(e0, c->stream);
-      launch_coal(c->t, c->precision, p, c->scratch, 5.0, 1, plan, c->stream);
+      launch_coal(c->t, c->precision, p, c->scratch, 5.0, kTuneSteps, plan, c->stream);
       cudaEventRecord(e1, c->stream);
       cudaEventSynchronize(e1);
       float ms = 0.f;
