@@ -304,18 +304,22 @@ static int step_sweep(const point_ctx* P, double* M, double dt, double B, double
             }
           }
           if (!(C * (xi + xj) > 0.0)) continue;
+          const double dM = C * (xi + xj);
+          /* [reading] the product bin may be bin j itself (product species b, k = j): that bin
+           * loses C x_j and receives dM = C (x_i + x_j) before the flux, so its content is
+           * M_j + C x_i, formed as that sum (not as a difference of two large terms), and it
+           * is filled before any clamping */
+          const int into_j = (cs == sb && k == j);
           if (sa == sb && i == j) {
             M[sa * n + i] -= 2.0 * C * xi;
           } else {
             M[sa * n + i] -= C * xi;
-            M[sb * n + j] -= C * xj;
+            if (!into_j) M[sb * n + j] -= C * xj;
           }
-          /* the product bin may be bin j itself: it is filled before any clamping */
-          const double dM = C * (xi + xj);
           if (k >= n - 1) {
-            M[cs * n + (n - 1)] += dM;
+            M[cs * n + (n - 1)] = into_j ? M[sb * n + j] + C * xi : M[cs * n + (n - 1)] + dM;
           } else {
-            const double g_k = M[cs * n + k] + dM;
+            const double g_k = into_j ? M[sb * n + j] + C * xi : M[cs * n + k] + dM;
             const double F = bott_flux(dM, g_k, M[cs * n + k + 1], c);
             M[cs * n + k] = g_k - F;
             M[cs * n + k + 1] += F;
