@@ -118,6 +118,10 @@ static double bott_flux(double dM, double g_k, double M_k1, double c) {
   double F;
   if (x1 == 0.0)
     F = dM * c;
+  else if (isinf(x1))
+    /* [reading] rho overflowed (g_k far below M_k1): the flux takes its limit as x1 grows,
+     * all of dM for c > 0 and nothing for c = 0 */
+    F = c > 0.0 ? dM : 0.0;
   else
     F = dM * exp(0.5 * x1) * (-expm1(-c * x1)) / x1;
   if (F < 0.0) F = 0.0;
@@ -290,17 +294,21 @@ static int step_sweep(const point_ctx* P, double* M, double dt, double B, double
           const int k = P->kidx[i * n + j];
           const double c = P->cfrac[i * n + j];
           double C;
+          /* [reading] the bin whose cap decides C gives up all its mass: it becomes exactly 0,
+           * the exact value of M - (M / x) x, rather than that difference's rounding residue
+           * (a residue in an emptied bin would later steer the logarithm of Bott's flux) */
+          int emptied = 0; /* 1: bin i, 2: bin j */
           if (sa == sb && i == j) {
             C = 0.5 * kern(P, a, i, b, j) * Ni * Nj * dt;
             const double cap = M[sa * n + i] / (2.0 * xi);
-            if (C > cap) { C = cap; limited = 1; }
+            if (C > cap) { C = cap; limited = 1; emptied = 1; }
           } else {
             C = kern(P, a, i, b, j) * Ni * Nj * dt;
             const double capi = M[sa * n + i] / xi;
-            if (C > capi) { C = capi; limited = 1; }
+            if (C > capi) { C = capi; limited = 1; emptied = 1; }
             if (!(cs == sb && k == j)) {
               const double capj = M[sb * n + j] / xj;
-              if (C > capj) { C = capj; limited = 1; }
+              if (C > capj) { C = capj; limited = 1; emptied = 2; }
             }
           }
           if (!(C * (xi + xj) > 0.0)) continue;
@@ -311,10 +319,10 @@ static int step_sweep(const point_ctx* P, double* M, double dt, double B, double
            * is filled before any clamping */
           const int into_j = (cs == sb && k == j);
           if (sa == sb && i == j) {
-            M[sa * n + i] -= 2.0 * C * xi;
+            M[sa * n + i] = emptied ? 0.0 : M[sa * n + i] - 2.0 * C * xi;
           } else {
-            M[sa * n + i] -= C * xi;
-            if (!into_j) M[sb * n + j] -= C * xj;
+            M[sa * n + i] = emptied == 1 ? 0.0 : M[sa * n + i] - C * xi;
+            if (!into_j) M[sb * n + j] = emptied == 2 ? 0.0 : M[sb * n + j] - C * xj;
           }
           if (k >= n - 1) {
             M[cs * n + (n - 1)] = into_j ? M[sb * n + j] + C * xi : M[cs * n + (n - 1)] + dM;
