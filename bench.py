@@ -250,9 +250,9 @@ def time_steps(fc, ds, w, steps, warmup, stream, torch, barrier=None):
     return ms, fc.stats()
 
 
-def run_form(pkg, torch, w, precision, steps, warmup, graph=False):
+def run_form(pkg, torch, w, precision, steps, warmup, graph=False, mode=0):
     """Time one form on one workload; returns a dict with value, kernel time and work."""
-    with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
+    with pkg.FsbmCoal(w.cfg(), precision=precision, mode=mode) as fc:
         ds = fc.upload(w.state(copy=False))
         fc.autotune(ds)
         fc.set_graph(graph)
@@ -405,11 +405,24 @@ def main():
         r32 = run_form(pkg, torch, st32, pkg.FSBM_FP32_SPLIT, 2, 3, graph=True)
         st64 = synth.subset(st32, np.arange(1000))
         r64 = run_form(pkg, torch, st64, pkg.FSBM_FP64, 1, 3)
+        # the ragged batch: 33 to 264 bins (four grids), 1 to 5 species, tau = 1e-12
+        rag = synth.config4(n_points=200_000, seed=4001)
+        rrag = run_form(pkg, torch, rag, pkg.FSBM_FP32_SPLIT, 2, 3, graph=True)
+        # Bott's in-place order (SWEEP), FP64, one thread per point, on a sample of the domain
+        sw = synth.conus_sample(20_000, 0, seed=8)
+        rsw = run_form(pkg, torch, sw, pkg.FSBM_FP64, 1, 3, mode=pkg.FSBM_SWEEP)
         for key, rr, ww, pr in (("stress_264bin_fp32_split_graph", r32, st32, 1),
-                                ("stress_264bin_fp64", r64, st64, 0)):
+                                ("stress_264bin_fp64", r64, st64, 0),
+                                ("ragged_33to264bin_fp32_split_graph", rrag, rag, 1),
+                                ("conus_33bin_fp64_sweep_20k", rsw, sw, 0)):
             rr["points"] = ww.n_points
             kms = rr.get("coal_ms") or rr.get("step_ms_graph")
-            rr["alu_frac"] = (pairs_per_active(ww) * ww.n_steps / (kms / 1e3)) / alu_peak_pairs(pr, sm_mhz)
+            if "sweep" in key:  # another algorithm (CUDA's log/exp/expm1, divisions): no pair-op model
+                rr["alu_frac"] = None
+            else:
+                rr["alu_frac"] = (pairs_per_active(ww) * ww.n_steps / (kms / 1e3)) / alu_peak_pairs(pr, sm_mhz)
+            if "ragged" in key:
+                rr["pairs_basis"] = "every bin of every stored species; the 1e-12 range cut-off skips some"
             forms[key] = rr
         fr = forms["conus_33bin_fp32_split_graph" if precision == 0 else "conus_33bin_fp64"]
         kms = fr.get("coal_ms") or fr.get("step_ms_graph")

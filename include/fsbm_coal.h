@@ -72,6 +72,19 @@ typedef enum {
                            limiter ratios, update and renormalisation             */
 } fsbm_precision;
 
+/* The order in which a step applies its pair transfers. Both use Bott's flux (Bott 1998), the
+ * method of the routine the paper ports (coal_bott_new, Sec. III, Listing 1). */
+typedef enum {
+  FSBM_PAIRWISE = 0,    /* every pair reads the start-of-step spectrum (Jacobi form) with
+                           one limiter ratio per bin; order-independent, parallel in a point */
+  FSBM_SWEEP = 1        /* Bott's in-place order: species pairs (a <= b), i ascending, j
+                           ascending (j >= i for a = b), each pair reading the spectrum its
+                           predecessors left, with per-pair caps C x_i <= M_i and
+                           C x_j <= M_j (none on bin j when the product lands there; 2 C x_i
+                           <= M_i on the diagonal). One thread per point, the paper's own
+                           mapping (Sec. V-B). FP64 only.                                  */
+} fsbm_mode;
+
 /* Per-point status bits written by fsbm_coal_step. */
 enum {
   FSBM_ST_LIMITED = 1,   /* the loss limiter fired (lambda < 1) in some bin and step   */
@@ -97,7 +110,9 @@ typedef struct {
   double active_rel_threshold;  /* tau in [0, 1): active range cut-off relative to the
                                    species' largest bin                                    */
   int32_t precision;            /* fsbm_precision                                         */
-  int32_t mode;                 /* 0 = pairwise; other values: FSBM_E_UNSUPPORTED          */
+  int32_t mode;                 /* fsbm_mode: FSBM_PAIRWISE or FSBM_SWEEP (FP64 only;
+                                   FSBM_SWEEP with FSBM_FP32_SPLIT: FSBM_E_UNSUPPORTED;
+                                   any other value: FSBM_E_ARG)                            */
 } fsbm_coal_config;
 
 typedef struct {                /* device pointers, caller-owned                          */

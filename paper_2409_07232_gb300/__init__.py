@@ -15,6 +15,8 @@ from . import binding
 from .binding import (  # noqa: F401
     FSBM_FP32_SPLIT,
     FSBM_FP64,
+    FSBM_PAIRWISE,
+    FSBM_SWEEP,
     FSBM_ST_BADINPUT,
     FSBM_ST_INACTIVE,
     FSBM_ST_LIMITED,
@@ -53,7 +55,8 @@ class FsbmCoal:
     [n][n]), product (or None), t_min_K and active_rel_threshold.
     """
 
-    def __init__(self, cfg: dict, precision: int = FSBM_FP64, stream=None, device: int = 0):
+    def __init__(self, cfg: dict, precision: int = FSBM_FP64, stream=None, device: int = 0,
+                 mode: int = FSBM_PAIRWISE):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("FsbmCoal needs a CUDA device")
@@ -64,7 +67,8 @@ class FsbmCoal:
         self.precision = precision
         self._cfg, self._keep = binding.make_config(
             cfg["n_species"], cfg["bins_per_grid"], cfg["x0_g"], cfg["alpha"], cfg["kernels"],
-            cfg.get("product"), cfg.get("t_min_K", 223.15), cfg.get("active_rel_threshold", 0.0), precision)
+            cfg.get("product"), cfg.get("t_min_K", 223.15), cfg.get("active_rel_threshold", 0.0), precision,
+            mode)
         self.ctx = fsbm_coal_init(self._cfg, self.stream.cuda_stream)
 
     @property

@@ -27,6 +27,8 @@ FSBM_E_TIMEOUT = -4
 FSBM_E_UNSUPPORTED = -5
 FSBM_FP64 = 0
 FSBM_FP32_SPLIT = 1
+FSBM_PAIRWISE = 0
+FSBM_SWEEP = 1
 FSBM_ST_LIMITED = 1
 FSBM_ST_BADINPUT = 2
 FSBM_ST_INACTIVE = 4

@@ -16,9 +16,13 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsbm_coal.so")
 HEADER = os.path.join(ROOT, "include", "fsbm_coal.h")
-SOURCES = ["compact.cu", "coal_kernel.cu", "fsbm_coal.cu"]
+SOURCES = ["compact.cu", "coal_kernel.cu", "sweep_kernel.cu", "fsbm_coal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
+# The SWEEP kernel rounds every product and sum separately, as the C oracle does: its in-place
+# updates cancel (a bin loses C x_j and regains C (x_i + x_j)), so a fused multiply-add there
+# changes results far beyond one rounding.
+EXTRA = {"sweep_kernel.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -43,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([_nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([_nvcc(), *ARCH, *FLAGS, *EXTRA.get(src, []), "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -822,11 +822,13 @@ size_t coal_smem_bytes(const Tables& t, int precision) {
 }
 
 cudaError_t coal_plan(const Tables& t, int precision, int block_dim, int n_sms, CoalLaunch* out) {
+  if (t.mode == 1) return sweep_plan(block_dim, n_sms, out);
   return precision == 0 ? plan_t<double>(t, block_dim, n_sms, out) : plan_t<float>(t, block_dim, n_sms, out);
 }
 
 cudaError_t launch_coal(const Tables& t, int precision, const PointsDev& p, const Scratch& s, double dt,
                         int n_steps, const CoalLaunch& plan, cudaStream_t stream) {
+  if (t.mode == 1) return launch_sweep(t, p, s, dt, n_steps, plan, stream);
   int nmax = 0;
   for (int g = 0; g < t.G; ++g) nmax = t.g[g].n > nmax ? t.g[g].n : nmax;
   if (precision == 0)

@@ -293,7 +293,9 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
       !cfg->kernels)
     return bail(FSBM_E_ARG);
   if (cfg->precision != FSBM_FP64 && cfg->precision != FSBM_FP32_SPLIT) return bail(FSBM_E_ARG);
-  if (cfg->mode != 0) return bail(FSBM_E_UNSUPPORTED);
+  // mode 1 (SWEEP) is Bott's in-place order, FP64 only
+  if (cfg->mode != 0 && cfg->mode != 1) return bail(FSBM_E_ARG);
+  if (cfg->mode == 1 && cfg->precision != FSBM_FP64) return bail(FSBM_E_UNSUPPORTED);
   if (!std::isfinite(cfg->t_min_K) || !(cfg->active_rel_threshold >= 0.0) || !(cfg->active_rel_threshold < 1.0))
     return bail(FSBM_E_ARG);
   c->S = S;
@@ -301,6 +303,7 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
   c->precision = cfg->precision;
   c->stream = static_cast<cudaStream_t>(stream);
   c->t.S = S;
+  c->t.mode = cfg->mode;
   c->t.G = G;
   c->t.t_min = cfg->t_min_K;
   c->t.tau = cfg->active_rel_threshold;
@@ -374,6 +377,7 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
     if ((st = upload(c, x, &gd.x64)) != FSBM_OK || (st = upload(c, x32, &gd.x32)) != FSBM_OK ||
         (st = upload(c, invx, &gd.invx64)) != FSBM_OK || (st = upload(c, invx32, &gd.invx32)) != FSBM_OK ||
         (st = upload(c, cd, &gd.cd64)) != FSBM_OK || (st = upload(c, cd32, &gd.cd32)) != FSBM_OK ||
+        (st = upload(c, kap, &gd.kapd)) != FSBM_OK ||
         (st = upload(c, Kd, &gd.Kd64)) != FSBM_OK || (st = upload(c, Kd32, &gd.Kd32)) != FSBM_OK ||
         (st = upload(c, Kr, &gd.Kr64)) != FSBM_OK || (st = upload(c, Kr32, &gd.Kr32)) != FSBM_OK)
       return bail(st);
@@ -386,7 +390,7 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess)
       return bail(FSBM_E_CUDA);
-    if (coal_smem_bytes(c->t, c->precision) + 1024 > (size_t)optin) return bail(FSBM_E_UNSUPPORTED);
+    if (c->t.mode == 0 && coal_smem_bytes(c->t, c->precision) + 1024 > (size_t)optin) return bail(FSBM_E_UNSUPPORTED);
   }
   {
     // tables of the FP64 logarithm and exponential (Tang's table-driven methods), in long double

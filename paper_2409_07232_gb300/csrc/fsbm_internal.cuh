@@ -38,6 +38,7 @@ struct GridDev {
   int kappa_max;                  // kappa[0]
   int d_lo[kMaxKappa + 1];        // D_kappa = {d : kappa[d] = kappa} = [d_lo, d_hi]
   int d_hi[kMaxKappa + 1];
+  const int* kapd;                // kappa[d], d = 0..n-1 (the per-pair lookup of the SWEEP form)
   const double* x64;
   const float* x32;
   const double* invx64;
@@ -53,6 +54,7 @@ struct GridDev {
 struct Tables {
   int S;
   int G;
+  int mode;                       // 0 pairwise (Jacobi), 1 SWEEP (Bott's in-place order, FP64)
   double t_min;
   double tau;
   int8_t product[kMaxSpecies * kMaxSpecies];
@@ -98,6 +100,10 @@ size_t coal_smem_bytes(const Tables& t, int precision);  // dynamic shared memor
 cudaError_t coal_plan(const Tables& t, int precision, int block_dim, int n_sms, CoalLaunch* out);
 cudaError_t launch_coal(const Tables& t, int precision, const PointsDev& p, const Scratch& s, double dt,
                         int n_steps, const CoalLaunch& plan, cudaStream_t stream);
+// sweep_kernel.cu: the SWEEP form, one thread per point (launched by launch_coal when mode = 1)
+cudaError_t sweep_plan(int block_dim, int n_sms, CoalLaunch* out);
+cudaError_t launch_sweep(const Tables& t, const PointsDev& p, const Scratch& s, double dt, int n_steps,
+                         const CoalLaunch& plan, cudaStream_t stream);
 // Largest errors of the FP64 helpers over a fixed sweep of arguments (written to out[0..4] on
 // device): fsbm_log (absolute, relative where |ln x| > 1), fsbm_exp, the e^y - 1 of
 // fsbm_exp_em1 (relative, against CUDA's log, exp, expm1), fsbm_rsqrt and fsbm_rcp (relative).

@@ -217,7 +217,13 @@ def test_argument_errors():
     bad["product"] = np.array([[3]], np.int8)
     with pytest.raises(pkg.FsbmError):
         pkg.FsbmCoal(bad)
-    c, keep = pkg.binding.make_config(1, cfg["bins_per_grid"], cfg["x0_g"], cfg["alpha"], cfg["kernels"], mode=1)
+    # an unknown mode is an argument error; SWEEP exists in FP64 only
+    c, keep = pkg.binding.make_config(1, cfg["bins_per_grid"], cfg["x0_g"], cfg["alpha"], cfg["kernels"], mode=2)
+    with pytest.raises(pkg.FsbmError) as e:
+        pkg.binding.fsbm_coal_init(c)
+    assert e.value.status == pkg.binding.FSBM_E_ARG
+    c, keep = pkg.binding.make_config(1, cfg["bins_per_grid"], cfg["x0_g"], cfg["alpha"], cfg["kernels"],
+                                      precision=pkg.FSBM_FP32_SPLIT, mode=pkg.FSBM_SWEEP)
     with pytest.raises(pkg.FsbmError) as e:
         pkg.binding.fsbm_coal_init(c)
     assert e.value.status == pkg.binding.FSBM_E_UNSUPPORTED
