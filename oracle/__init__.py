@@ -60,6 +60,9 @@ class _Config(ctypes.Structure):
         ("product", ctypes.c_void_p),
         ("t_min_K", ctypes.c_double),
         ("active_rel_threshold", ctypes.c_double),
+        ("kernels_p2", ctypes.c_void_p),
+        ("p1_hpa", ctypes.c_double),
+        ("p2_hpa", ctypes.c_double),
     ]
 
 
@@ -71,6 +74,7 @@ class _State(ctypes.Structure):
         ("species_mask", ctypes.c_void_p),
         ("cloudy", ctypes.c_void_p),
         ("temperature", ctypes.c_void_p),
+        ("pressure", ctypes.c_void_p),
         ("mass_budget", ctypes.c_void_p),
         ("mass_error", ctypes.c_void_p),
         ("status", ctypes.c_void_p),
@@ -118,9 +122,11 @@ class Oracle:
 
         ``cfg``: mapping with n_species, bins_per_grid, x0_g, alpha, kernels (float64,
         [grid][pair][n][n] flattened in grid order), product ([S,S] int8), t_min_K,
-        active_rel_threshold. ``state``: mapping with spectra (float64, modified in place),
-        offset (int64), grid_id (uint8), species_mask (uint8), optional cloudy (uint8) and
-        temperature (float32). Returns dict(mass_budget, mass_error, status, min_rel_preclamp).
+        active_rel_threshold, optional kernels_p2 (same layout as kernels), p1_hpa and p2_hpa
+        (the pressures of the two tables). ``state``: mapping with spectra (float64, modified
+        in place), offset (int64), grid_id (uint8), species_mask (uint8), optional cloudy
+        (uint8), temperature (float32) and pressure (float32, hPa). Returns dict(mass_budget,
+        mass_error, status, min_rel_preclamp).
         """
         bins = np.ascontiguousarray(cfg["bins_per_grid"], np.int32)
         x0 = np.ascontiguousarray(cfg["x0_g"], np.float64)
@@ -131,8 +137,14 @@ class Oracle:
         npairs = S * (S + 1) // 2
         if kern.size != npairs * int(np.sum(bins.astype(np.int64) ** 2)):
             raise ValueError("kernels: wrong size")
+        kern2 = cfg.get("kernels_p2")
+        if kern2 is not None:
+            kern2 = np.ascontiguousarray(kern2, np.float64).reshape(-1)
+            if kern2.size != kern.size:
+                raise ValueError("kernels_p2: wrong size")
         c = _Config(S, len(bins), bins.ctypes.data, x0.ctypes.data, alpha.ctypes.data, kern.ctypes.data,
-                    prod.ctypes.data, float(cfg["t_min_K"]), float(cfg["active_rel_threshold"]))
+                    prod.ctypes.data, float(cfg["t_min_K"]), float(cfg["active_rel_threshold"]), _p(kern2),
+                    float(cfg.get("p1_hpa", 750.0)), float(cfg.get("p2_hpa", 500.0)))
         spectra = state["spectra"]
         if spectra.dtype != np.float64 or not spectra.flags.c_contiguous:
             raise ValueError("spectra must be contiguous float64 (modified in place)")
@@ -144,6 +156,8 @@ class Oracle:
         cloudy = None if cloudy is None else np.ascontiguousarray(cloudy, np.uint8)
         temp = state.get("temperature")
         temp = None if temp is None else np.ascontiguousarray(temp, np.float32)
+        pres = state.get("pressure")
+        pres = None if pres is None else np.ascontiguousarray(pres, np.float32)
         out = dict(
             mass_budget=np.zeros(npts, np.float64),
             mass_error=np.zeros(npts, np.float64),
@@ -151,7 +165,7 @@ class Oracle:
             min_rel_preclamp=np.zeros(npts, np.float64),
         )
         s = _State(spectra.ctypes.data, offset.ctypes.data, grid_id.ctypes.data, mask.ctypes.data,
-                   _p(cloudy), _p(temp), out["mass_budget"].ctypes.data, out["mass_error"].ctypes.data,
+                   _p(cloudy), _p(temp), _p(pres), out["mass_budget"].ctypes.data, out["mass_error"].ctypes.data,
                    out["status"].ctypes.data, out["min_rel_preclamp"].ctypes.data)
         rc = self.lib.oracle_coal_step(ctypes.byref(c), ctypes.byref(s), npts, float(dt), int(n_steps),
                                        int(mode), int(n_threads))

@@ -90,6 +90,8 @@ typedef struct {
   const int32_t* kidx;          /* [n*n]                                        */
   const double* cfrac;          /* [n*n]                                        */
   const double* K;              /* this grid's kernels [pair][n][n]             */
+  const double* K2;             /* ... at the second pressure level, or NULL    */
+  double w;                     /* weight of K2 at this point's pressure        */
   const int8_t* product;        /* [S][S]                                       */
   double tau;
 } point_ctx;
@@ -97,12 +99,21 @@ typedef struct {
 /* Collection kernel of particle (a, bin i) with particle (b, bin j).
  * a < b: K_ab[i][j]; a > b: K_ba[j][i]; a == b: the upper-triangle entry
  * K_aa[min(i,j)][max(i,j)] ([reading] a same-species table is read as symmetric). */
-static double kern(const point_ctx* P, int a, int i, int b, int j) {
+static double kern_table(const point_ctx* P, const double* K, int a, int i, int b, int j) {
   const size_t nn = (size_t)P->n * (size_t)P->n;
-  if (a < b) return P->K[(size_t)pair_index(P->S, a, b) * nn + (size_t)i * P->n + j];
-  if (a > b) return P->K[(size_t)pair_index(P->S, b, a) * nn + (size_t)j * P->n + i];
+  if (a < b) return K[(size_t)pair_index(P->S, a, b) * nn + (size_t)i * P->n + j];
+  if (a > b) return K[(size_t)pair_index(P->S, b, a) * nn + (size_t)j * P->n + i];
   const int lo = i < j ? i : j, hi = i < j ? j : i;
-  return P->K[(size_t)pair_index(P->S, a, a) * nn + (size_t)lo * P->n + hi];
+  return K[(size_t)pair_index(P->S, a, a) * nn + (size_t)lo * P->n + hi];
+}
+
+/* The collection kernel of species a bin i with species b bin j at this point: the table
+ * entry, or the two pressure levels' entries combined with the point's weight w. */
+static double kern(const point_ctx* P, int a, int i, int b, int j) {
+  const double k1 = kern_table(P, P->K, a, i, b, j);
+  if (!P->K2) return k1;
+  const double k2 = kern_table(P, P->K2, a, i, b, j);
+  return k1 + P->w * (k2 - k1);
 }
 
 /* Bott's flux of the combined mass dM from bin k into bin k+1 of the product species.
@@ -382,6 +393,10 @@ int oracle_coal_step(const oracle_config* cfg, const oracle_state* st, int64_t n
   int32_t* kg[MAX_GRIDS] = {0};
   double* cg[MAX_GRIDS] = {0};
   const double* Kg[MAX_GRIDS] = {0};
+  const double* K2g[MAX_GRIDS] = {0};
+  if (cfg->kernels_p2 &&
+      (!isfinite(cfg->p1_hpa) || !isfinite(cfg->p2_hpa) || cfg->p1_hpa == cfg->p2_hpa))
+    return -1;
   size_t koff = 0;
   int rc = 0;
   const int npairs = S * (S + 1) / 2;
@@ -395,6 +410,7 @@ int oracle_coal_step(const oracle_config* cfg, const oracle_state* st, int64_t n
     for (int k = 0; k < n; ++k) xg[g][k] = bin_mass(cfg->x0_g[g], cfg->alpha[g], k);
     if (oracle_grid_tables(n, cfg->x0_g[g], cfg->alpha[g], kg[g], cg[g]) != 0) { rc = -1; break; }
     Kg[g] = cfg->kernels + koff;
+    K2g[g] = cfg->kernels_p2 ? cfg->kernels_p2 + koff : NULL;
     koff += (size_t)npairs * n * n;
   }
 
@@ -428,6 +444,19 @@ int oracle_coal_step(const oracle_config* cfg, const oracle_state* st, int64_t n
       P.kidx = kg[g];
       P.cfrac = cg[g];
       P.K = Kg[g];
+      P.K2 = K2g[g];
+      P.w = 0.0;
+      if (P.K2 && st->pressure) {
+        const double pr = (double)st->pressure[p];
+        if (!isfinite(pr)) {
+          st->status[p] = ORACLE_ST_BADINPUT;
+          continue;
+        }
+        double w = (cfg->p1_hpa - pr) / (cfg->p1_hpa - cfg->p2_hpa);
+        if (w < 0.0) w = 0.0;
+        if (w > 1.0) w = 1.0;
+        P.w = w;
+      }
       P.product = cfg->product;
       P.tau = cfg->active_rel_threshold;
       const int64_t len = st->offset[p + 1] - st->offset[p];

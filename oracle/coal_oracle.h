@@ -12,8 +12,8 @@
  * stochastic collection equation, in the pairwise (Jacobi) form: every bin pair reads
  * start-of-step values, losses are limited by a per-bin ratio, and the combined mass
  * of a pair is split between the two mass bins that bracket it with Bott's
- * exponential-profile flux. The readings taken where the paper is silent are listed in
- * the design doc and repeated beside the code that implements them.
+ * exponential-profile flux. Each reading taken where the paper is silent is marked
+ * [reading] beside the code that implements it.
  *
  * Units are CGS: bin mass content M in g cm^-3, particle mass x in g, kernel K in
  * cm^3 s^-1, dt in s.
@@ -45,6 +45,15 @@ typedef struct {
   const int8_t* product;          /* [S][S] product species of a collision            */
   double t_min_K;                 /* collisions only where T > t_min_K                */
   double active_rel_threshold;    /* tau_act                                          */
+  /* Pressure dependence of the kernels (Sec. V-A, Listing 2: every collision array is
+   * formed from a 750 mb and a 500 mb table). kernels_p2 == NULL: `kernels` is used as is.
+   * Otherwise `kernels` holds the tables at pressure p1_hpa and kernels_p2 (same layout)
+   * those at p2_hpa, and a point at pressure p uses
+   *   K = K1 + w (K2 - K1),  w = (p1 - p) / (p1 - p2) clamped to [0, 1]
+   * [reading: linear in pressure between the two levels, constant outside them; the
+   * paper elides the formula]. A point without a pressure (pressure == NULL) is at p1. */
+  const double* kernels_p2;
+  double p1_hpa, p2_hpa;
 } oracle_config;
 
 typedef struct {
@@ -54,6 +63,7 @@ typedef struct {
   const uint8_t* species_mask;    /* [n_points] bit a set: species a stored           */
   const uint8_t* cloudy;          /* [n_points] or NULL                               */
   const float* temperature;       /* [n_points] or NULL                               */
+  const float* pressure;          /* [n_points] hPa, or NULL (see kernels_p2)         */
   double* mass_budget;            /* [n_points] out: B of the first step              */
   double* mass_error;             /* [n_points] out: max over steps of |sum M'-B|/B   */
   int32_t* status;                /* [n_points] out                                   */

@@ -22,4 +22,5 @@ from .workloads import (  # noqa: F401
     conus_sample,
     custom_points,
     subset,
+    with_pressure_levels,
 )

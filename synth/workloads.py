@@ -157,6 +157,9 @@ class Workload:
     species_mask: np.ndarray               # uint8 [P]
     cloudy: Optional[np.ndarray] = None    # uint8 [P]
     temperature: Optional[np.ndarray] = None  # float32 [P]
+    kernels_p2: Optional[np.ndarray] = None   # float64, same layout: tables at p_levels[1]
+    p_levels: tuple = (750.0, 500.0)          # hPa of `kernels` and of `kernels_p2`
+    pressure: Optional[np.ndarray] = None     # float32 [P] hPa
     dt: float = 1.0
     n_steps: int = 1
     t_min_K: float = T_MIN_K
@@ -169,16 +172,20 @@ class Workload:
         return len(self.grid_id)
 
     def cfg(self) -> dict:
-        return dict(n_species=self.n_species, n_grids=len(self.bins_per_grid),
-                    bins_per_grid=np.asarray(self.bins_per_grid, np.int32),
-                    x0_g=np.asarray(self.x0_g, np.float64), alpha=np.asarray(self.alpha, np.float64),
-                    kernels=self.kernels, product=self.product, t_min_K=self.t_min_K,
-                    active_rel_threshold=self.tau)
+        c = dict(n_species=self.n_species, n_grids=len(self.bins_per_grid),
+                 bins_per_grid=np.asarray(self.bins_per_grid, np.int32),
+                 x0_g=np.asarray(self.x0_g, np.float64), alpha=np.asarray(self.alpha, np.float64),
+                 kernels=self.kernels, product=self.product, t_min_K=self.t_min_K,
+                 active_rel_threshold=self.tau)
+        if self.kernels_p2 is not None:
+            c.update(kernels_p2=self.kernels_p2, p1_hpa=float(self.p_levels[0]), p2_hpa=float(self.p_levels[1]))
+        return c
 
     def state(self, copy: bool = True) -> dict:
         sp = self.spectra.copy() if copy else self.spectra
         return dict(spectra=sp, offset=self.offset, grid_id=self.grid_id,
-                    species_mask=self.species_mask, cloudy=self.cloudy, temperature=self.temperature)
+                    species_mask=self.species_mask, cloudy=self.cloudy, temperature=self.temperature,
+                    pressure=self.pressure)
 
     def stored_species(self, p: int):
         m = int(self.species_mask[p])
@@ -412,5 +419,28 @@ def subset(w: Workload, idx) -> Workload:
         offset=off, grid_id=w.grid_id[idx].copy(), species_mask=w.species_mask[idx].copy(),
         cloudy=None if w.cloudy is None else w.cloudy[idx].copy(),
         temperature=None if w.temperature is None else w.temperature[idx].copy(),
+        kernels_p2=w.kernels_p2, p_levels=w.p_levels,
+        pressure=None if w.pressure is None else w.pressure[idx].copy(),
         dt=w.dt, n_steps=w.n_steps, t_min_K=w.t_min_K, tau=w.tau, precision=w.precision,
         meta=dict(w.meta))
+
+
+def with_pressure_levels(w: Workload, seed: int = 17, p_levels=(750.0, 500.0), p_range=(300.0, 900.0)) -> Workload:
+    """A copy of ``w`` whose kernel tables come at two pressure levels and whose points carry a
+    pressure (FSBM forms every collision table from a 750 mb and a 500 mb table).
+
+    The table at p_levels[0] is ``w.kernels``. The one at p_levels[1] is the same table with
+    every fall speed sqrt(p0 / p1) times faster (air density scales with pressure at fixed
+    temperature, terminal speed as its inverse square root), so every entry scales by that
+    factor, times a seeded per-entry change of the collision efficiency of up to +-10 %.
+    Point pressures are drawn uniformly from ``p_range`` hPa, which reaches past both levels.
+    """
+    rng = np.random.default_rng(seed)
+    f = math.sqrt(p_levels[0] / p_levels[1])
+    k2 = w.kernels * f * rng.uniform(0.9, 1.1, size=w.kernels.shape)
+    out = subset(w, np.arange(w.n_points))
+    out.name = w.name + "+p"
+    out.kernels_p2 = k2.astype(np.float64)
+    out.p_levels = (float(p_levels[0]), float(p_levels[1]))
+    out.pressure = rng.uniform(p_range[0], p_range[1], size=w.n_points).astype(np.float32)
+    return out

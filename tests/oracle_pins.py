@@ -319,6 +319,48 @@ def pin_sweep_caps_empty_exactly(orc):
     assert np.count_nonzero((sp == 0.0) & (w.spectra > 0.0)) > 0
 
 
+def pin_pressure_levels(orc):
+    """Kernels at two pressure levels (Sec. V-A, Listing 2: each collision table is formed from
+    a 750 mb and a 500 mb table; the reading: linear in pressure between them, constant
+    outside). Checked without the interpolation formula: a point at or beyond 750 mb steps
+    exactly as with the 750 mb table alone, one at or beyond 500 mb as with the 500 mb table
+    alone; in the one-bin constant-kernel case, whose step is linear in K, the midpoint
+    pressure moves the average of the two levels' masses, and a quarter of the way the
+    quarter-weighted one."""
+    n, x0, alpha = synth.mass_grid(1)
+    x = bin_masses(n, x0, alpha)
+    i, m, dt = 7, 3e-7, 0.5
+    c1, c2 = 2e-4, 5e-4
+    M = np.zeros(n)
+    M[i] = m
+    k1, k2 = synth.constant_kernel(n, c1), synth.constant_kernel(n, c2)
+
+    def one(kernels, k_p2=None, pressures=None):
+        w = synth.custom_points("lv", 1, [(n, x0, alpha)], kernels, [M] * len(pressures or [0]),
+                                [0] * len(pressures or [0]), [1] * len(pressures or [0]), dt, 1)
+        if k_p2 is not None:
+            w.kernels_p2 = np.asarray(k_p2, np.float64).reshape(-1)
+            w.pressure = np.asarray(pressures, np.float32)
+        sp, out = orc.run(w)
+        return sp.reshape(-1, n)
+
+    at1, at2 = one(k1)[0], one(k2)[0]
+    got = one(k1, k2, [750.0, 900.0, 500.0, 300.0, 625.0, 687.5])
+    assert np.array_equal(got[0], at1) and np.array_equal(got[1], at1)
+    assert np.allclose(got[2], at2, rtol=1e-15, atol=1e-15 * m) and np.array_equal(got[3], got[2])
+    moved1, moved2 = m - at1[i], m - at2[i]
+    assert np.isclose(moved1, c1 * (m / x[i]) ** 2 * x[i] * dt, rtol=1e-13)
+    assert np.isclose(m - got[4][i], 0.5 * (moved1 + moved2), rtol=1e-14)
+    assert np.isclose(m - got[5][i], 0.75 * moved1 + 0.25 * moved2, rtol=1e-14)
+    # and on a many-species, many-bin case: at 750 mb exactly the one-table run
+    w = synth.with_pressure_levels(synth.conus_sample(12, 0, seed=5), seed=6)
+    w.pressure[:] = 750.0
+    sp_lv, _ = orc.run(w)
+    w.kernels_p2, w.pressure = None, None
+    sp_one, _ = orc.run(w)
+    assert np.array_equal(sp_lv, sp_one)
+
+
 def pin_status(orc):
     n, x0, alpha = synth.mass_grid(1)
     K = synth.golovin_kernel(n, x0, alpha)
@@ -342,6 +384,6 @@ def pin_status(orc):
 
 
 FAST_PINS = [pin_identity_k0, pin_one_bin_constant, pin_single_pair, pin_mass_conservation,
-             pin_positivity, pin_number_nonincreasing, pin_scaling, pin_status]
+             pin_positivity, pin_number_nonincreasing, pin_scaling, pin_status, pin_pressure_levels]
 SLOW_PINS = [pin_grid_tables, pin_golovin, pin_constant, pin_sweep, pin_sweep_caps_empty_exactly]
 ALL_PINS = FAST_PINS + SLOW_PINS

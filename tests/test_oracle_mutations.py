@@ -27,8 +27,8 @@ MUTATIONS = [
     ("target bin one too high",
      "kidx[i * n + j] = k;", "kidx[i * n + j] = k + 1;"),
     ("cross-species kernel read transposed",
-     "if (a < b) return P->K[(size_t)pair_index(P->S, a, b) * nn + (size_t)i * P->n + j];",
-     "if (a < b) return P->K[(size_t)pair_index(P->S, a, b) * nn + (size_t)j * P->n + i];"),
+     "if (a < b) return K[(size_t)pair_index(P->S, a, b) * nn + (size_t)i * P->n + j];",
+     "if (a < b) return K[(size_t)pair_index(P->S, a, b) * nn + (size_t)j * P->n + i];"),
     ("Courant number measured from the top of the bin",
      "cfrac[i * n + j] = c;", "cfrac[i * n + j] = (c > 0.0 ? 1.0 - c : 0.0);"),
     ("profile centre at the top of the bin",
@@ -56,6 +56,13 @@ MUTATIONS = [
      "  if (F > dM) F = dM;\n", "\n"),
     ("top bin flux not suppressed",
      "  if (k >= n - 1) {\n    /* [reading]", "  if (k >= n) {\n    /* [reading]"),
+    ("pressure weight applied to the wrong level",
+     "return k1 + P->w * (k2 - k1);", "return k2 + P->w * (k1 - k2);"),
+    ("pressure weight measured from the wrong level",
+     "double w = (cfg->p1_hpa - pr) / (cfg->p1_hpa - cfg->p2_hpa);",
+     "double w = (pr - cfg->p2_hpa) / (cfg->p1_hpa - cfg->p2_hpa);"),
+    ("pressure weight not clamped beyond the second level",
+     "        if (w > 1.0) w = 1.0;\n", "\n"),
     ("requested loss counts only the same species",
      "for (int t = 0; t < ns; ++t)\n        for (int j = lo[t]; j <= hi[t]; ++j) acc +=",
      "for (int t = s; t <= s; ++t)\n        for (int j = lo[t]; j <= hi[t]; ++j) acc +="),
