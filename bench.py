@@ -411,10 +411,18 @@ def main():
         # Bott's in-place order (SWEEP), FP64, one thread per point, on a sample of the domain
         sw = synth.conus_sample(20_000, 0, seed=8)
         rsw = run_form(pkg, torch, sw, pkg.FSBM_FP64, 1, 3, mode=pkg.FSBM_SWEEP)
+        # kernels at two pressure levels (750 and 500 mb), per-point pressures: FP32 on the
+        # whole domain, FP64 on a sample
+        lv32 = synth.with_pressure_levels(w, seed=9)
+        rlv32 = run_form(pkg, torch, lv32, pkg.FSBM_FP32_SPLIT, 2, 3, graph=True)
+        lv64 = synth.with_pressure_levels(synth.conus_sample(50_000, 0, seed=10), seed=11)
+        rlv64 = run_form(pkg, torch, lv64, pkg.FSBM_FP64, 1, 3)
         for key, rr, ww, pr in (("stress_264bin_fp32_split_graph", r32, st32, 1),
                                 ("stress_264bin_fp64", r64, st64, 0),
                                 ("ragged_33to264bin_fp32_split_graph", rrag, rag, 1),
-                                ("conus_33bin_fp64_sweep_20k", rsw, sw, 0)):
+                                ("conus_33bin_fp64_sweep_20k", rsw, sw, 0),
+                                ("conus_33bin_fp32_split_graph_two_levels", rlv32, lv32, 1),
+                                ("conus_33bin_fp64_two_levels_50k", rlv64, lv64, 0)):
             rr["points"] = ww.n_points
             kms = rr.get("coal_ms") or rr.get("step_ms_graph")
             if "sweep" in key:  # another algorithm (CUDA's log/exp/expm1, divisions): no pair-op model

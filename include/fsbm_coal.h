@@ -113,6 +113,16 @@ typedef struct {
   int32_t mode;                 /* fsbm_mode: FSBM_PAIRWISE or FSBM_SWEEP (FP64 only;
                                    FSBM_SWEEP with FSBM_FP32_SPLIT: FSBM_E_UNSUPPORTED;
                                    any other value: FSBM_E_ARG)                            */
+  /* Kernels at two pressure levels (Sec. V-A, Listing 2: FSBM forms each collision table
+   * from a 750 mb and a 500 mb table). NULL: `kernels` is used as is and pressures are
+   * ignored. Otherwise `kernels` holds the tables at p1_hpa and kernels_p2 (host FP64, same
+   * layout, finite, >= 0) those at p2_hpa, and a point at pressure p collides with
+   *   K = K1 + w (K2 - K1),  w = (p1 - p) / (p1 - p2) clamped to [0, 1]
+   * (linear between the levels, constant outside; the paper elides the formula). The tables
+   * are read on demand per pair (Listing 4), one extra load and multiply-add each.         */
+  const double* kernels_p2;
+  double p1_hpa;                /* finite; p1_hpa != p2_hpa when kernels_p2 is set         */
+  double p2_hpa;
 } fsbm_coal_config;
 
 typedef struct {                /* device pointers, caller-owned                          */
@@ -128,6 +138,9 @@ typedef struct {                /* device pointers, caller-owned                
   double* mass_error;           /* [n_points] out: max over steps of |sum M' - B_s| / B_s
                                    before renormalisation                                  */
   int32_t* status;              /* [n_points] out: FSBM_ST_* bits                          */
+  const float* pressure;        /* [n_points] in hPa, read when the context has
+                                   kernels_p2; NULL = every point at p1_hpa; a non-finite
+                                   value marks the point FSBM_ST_BADINPUT                  */
 } fsbm_coal_state;
 
 /* Counters of the most recent step (read back with a stream synchronisation). */

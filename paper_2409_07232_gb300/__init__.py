@@ -45,7 +45,7 @@ class DeviceState:
         self.struct = binding.make_state(
             tensors["spectra"], tensors["offset"], tensors["grid_id"], tensors["species_mask"],
             tensors["mass_budget"], tensors["mass_error"], tensors["status"],
-            cloudy=tensors.get("cloudy"), temperature=tensors.get("temperature"))
+            cloudy=tensors.get("cloudy"), temperature=tensors.get("temperature"), pressure=tensors.get("pressure"))
 
 
 class FsbmCoal:
@@ -68,7 +68,7 @@ class FsbmCoal:
         self._cfg, self._keep = binding.make_config(
             cfg["n_species"], cfg["bins_per_grid"], cfg["x0_g"], cfg["alpha"], cfg["kernels"],
             cfg.get("product"), cfg.get("t_min_K", 223.15), cfg.get("active_rel_threshold", 0.0), precision,
-            mode)
+            mode, cfg.get("kernels_p2"), cfg.get("p1_hpa", 750.0), cfg.get("p2_hpa", 500.0))
         self.ctx = fsbm_coal_init(self._cfg, self.stream.cuda_stream)
 
     @property
@@ -94,6 +94,8 @@ class FsbmCoal:
             t["cloudy"] = torch.from_numpy(np.ascontiguousarray(state["cloudy"], np.uint8)).to(dev)
         if state.get("temperature") is not None:
             t["temperature"] = torch.from_numpy(np.ascontiguousarray(state["temperature"], np.float32)).to(dev)
+        if state.get("pressure") is not None:
+            t["pressure"] = torch.from_numpy(np.ascontiguousarray(state["pressure"], np.float32)).to(dev)
         torch.cuda.synchronize(dev)
         return DeviceState(t, n)
 
@@ -114,7 +116,8 @@ class FsbmCoal:
                                 np.ascontiguousarray(state["grid_id"], np.uint8),
                                 np.ascontiguousarray(state["species_mask"], np.uint8),
                                 out["mass_budget"], out["mass_error"], out["status"],
-                                cloudy=state.get("cloudy"), temperature=state.get("temperature"))
+                                cloudy=state.get("cloudy"), temperature=state.get("temperature"),
+                                pressure=state.get("pressure"))
         fsbm_coal_step_host(self.ctx, st, n, dt, n_steps)
         return out
 

@@ -61,6 +61,9 @@ class fsbm_coal_config(ctypes.Structure):
         ("active_rel_threshold", ctypes.c_double),
         ("precision", ctypes.c_int32),
         ("mode", ctypes.c_int32),
+        ("kernels_p2", ctypes.c_void_p),
+        ("p1_hpa", ctypes.c_double),
+        ("p2_hpa", ctypes.c_double),
     ]
 
 
@@ -75,6 +78,7 @@ class fsbm_coal_state(ctypes.Structure):
         ("mass_budget", ctypes.c_void_p),
         ("mass_error", ctypes.c_void_p),
         ("status", ctypes.c_void_p),
+        ("pressure", ctypes.c_void_p),
     ]
 
 
@@ -153,23 +157,26 @@ def _ptr(x):
 
 
 def make_config(n_species, bins_per_grid, x0_g, alpha, kernels, product=None, t_min_K=223.15,
-                active_rel_threshold=0.0, precision=FSBM_FP64, mode=0):
+                active_rel_threshold=0.0, precision=FSBM_FP64, mode=0, kernels_p2=None, p1_hpa=750.0,
+                p2_hpa=500.0):
     """Build an fsbm_coal_config from host arrays; returns (struct, keepalive)."""
     keep = dict(bins=np.ascontiguousarray(bins_per_grid, np.int32),
                 x0=np.ascontiguousarray(x0_g, np.float64), alpha=np.ascontiguousarray(alpha, np.float64),
                 kern=np.ascontiguousarray(kernels, np.float64).reshape(-1),
-                prod=None if product is None else np.ascontiguousarray(product, np.int8))
+                prod=None if product is None else np.ascontiguousarray(product, np.int8),
+                kern2=None if kernels_p2 is None else np.ascontiguousarray(kernels_p2, np.float64).reshape(-1))
     cfg = fsbm_coal_config(int(n_species), len(keep["bins"]), keep["bins"].ctypes.data, keep["x0"].ctypes.data,
                            keep["alpha"].ctypes.data, keep["kern"].ctypes.data, _ptr(keep["prod"]),
-                           float(t_min_K), float(active_rel_threshold), int(precision), int(mode))
+                           float(t_min_K), float(active_rel_threshold), int(precision), int(mode),
+                           _ptr(keep["kern2"]), float(p1_hpa), float(p2_hpa))
     return cfg, keep
 
 
 def make_state(spectra, offset, grid_id, species_mask, mass_budget, mass_error, status, cloudy=None,
-               temperature=None) -> fsbm_coal_state:
+               temperature=None, pressure=None) -> fsbm_coal_state:
     """Build an fsbm_coal_state from device tensors (or host arrays for the _host call)."""
     return fsbm_coal_state(_ptr(spectra), _ptr(offset), _ptr(grid_id), _ptr(species_mask), _ptr(cloudy),
-                           _ptr(temperature), _ptr(mass_budget), _ptr(mass_error), _ptr(status))
+                           _ptr(temperature), _ptr(mass_budget), _ptr(mass_error), _ptr(status), _ptr(pressure))
 
 
 def fsbm_coal_init(config: fsbm_coal_config, stream: int = 0) -> ctypes.c_void_p:

@@ -140,6 +140,8 @@ template <> struct Sel<double> {
   static __device__ const double* cd(const GridDev& g) { return g.cd64; }
   static __device__ const double* Kd(const GridDev& g) { return g.Kd64; }
   static __device__ const double* Kr(const GridDev& g) { return g.Kr64; }
+  static __device__ const double* Kd_d(const GridDev& g) { return g.Kd64_d; }
+  static __device__ const double* Kr_d(const GridDev& g) { return g.Kr64_d; }
 };
 template <> struct Sel<float> {
   static __device__ const float* x(const GridDev& g) { return g.x32; }
@@ -147,6 +149,8 @@ template <> struct Sel<float> {
   static __device__ const float* cd(const GridDev& g) { return g.cd32; }
   static __device__ const float* Kd(const GridDev& g) { return g.Kd32; }
   static __device__ const float* Kr(const GridDev& g) { return g.Kr32; }
+  static __device__ const float* Kd_d(const GridDev& g) { return g.Kd32_d; }
+  static __device__ const float* Kr_d(const GridDev& g) { return g.Kr32_d; }
 };
 
 // Running sums. The FP64 form adds each term in FP64. The FP32 form adds short runs of
@@ -365,16 +369,18 @@ template <> struct TargetOf<float> {
 // (the orientation's fields, the group's constants) is copied into registers first: the
 // loop then touches shared memory only for the two spectrum values, the limiter ratio and
 // the Courant number of its pair.
-template <typename T, bool LIMITED>
+// LEVELS: the point lies between two pressure levels; its kernel is K1 + wl (K2 - K1).
+template <typename T, bool LIMITED, bool LEVELS>
 __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T>& sm, const Orient& o_ref,
                                           const int* lo, const int* hi, int k, T dt, double B, const MathTabs& mt,
-                                          typename Num<T>::Sum* out_stay, typename Num<T>::Sum* out_up) {
+                                          T wl, typename Num<T>::Sum* out_stay, typename Num<T>::Sum* out_up) {
   const int n = G.n;
   const Orient o = o_ref;  // register copy
   const int dmin = o.dmin;
   const int kappa_max = G.kappa_max;
   Acc<T> stay, up;
   const T* __restrict__ Kd = Sel<T>::Kd(G) + o.table;
+  const T* __restrict__ Kdd = LEVELS ? Sel<T>::Kd_d(G) + o.table : nullptr;
   const T* __restrict__ Ns = sm.N + o.s * n;
   const T* __restrict__ Nl = sm.N + o.l * n;
   const T* __restrict__ Ms = sm.Mt + o.s * n;
@@ -418,7 +424,9 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
     // one pair (m - d, m): dM = C (x_i + x_m) = K N_m dt (M_i + N_i x_m) h phi; the table
     // entry of the same-species diagonal pair already holds h K = K / 2
     const int i = m - d;
-    T dM = __ldg(Kd + ko) * nl * fma(Ns[i], xl, Ms[i]);
+    T K = __ldg(Kd + ko);
+    if (LEVELS) K = fma(wl, __ldg(Kdd + ko), K);
+    T dM = K * nl * fma(Ns[i], xl, Ms[i]);
     if (LIMITED) dM *= min_nonneg(Ls[i], ll);
     if (pos(dM)) {
       const T c = cds[d];
@@ -448,7 +456,9 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
 template <typename T>
 struct StoreOf { using type = T; };
 
-template <typename T>
+// LEV: kernels at two pressure levels (a separate instantiation, so that the one-level kernel
+// keeps its registers and instructions)
+template <typename T, bool LEV>
 __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list, int32_t* counters, double dt,
                        int n_steps, int nmax) {
   using Store = typename StoreOf<T>::type;
@@ -482,6 +492,10 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
     const int64_t off = pd.offset[p];
     Store* spec = reinterpret_cast<Store*>(pd.spectra) + off;
     const int E = ns * n;
+    // kernels at two pressure levels: weight of the second at this point (0: the first alone)
+    const double wlev = LEV ? level_weight(t, pd, p) : 0.0;
+    const bool lev = LEV && wlev != 0.0;
+    const T wT = (T)wlev;
 
     if (tid == 0) {
       int q = 0;
@@ -587,10 +601,20 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
           for (int b = 0; b < ns; ++b) {
             const T* Kab = Kr + (size_t)(s_sp[a] * S + s_sp[b]) * n * n + i;
             const T* Nb = sm.N + b * n;
-            for (int j0 = s_lo[b]; j0 <= s_hi[b]; j0 += kLossRun) {
-              const int j1 = min(s_hi[b], j0 + kLossRun - 1);
-              for (int j = j0; j <= j1; ++j) acc.add(__ldg(Kab + (size_t)j * n) * Nb[j]);
-              acc.flush();
+            if (lev) {
+              const T* Kabd = Sel<T>::Kr_d(G) + (size_t)(s_sp[a] * S + s_sp[b]) * n * n + i;
+              for (int j0 = s_lo[b]; j0 <= s_hi[b]; j0 += kLossRun) {
+                const int j1 = min(s_hi[b], j0 + kLossRun - 1);
+                for (int j = j0; j <= j1; ++j)
+                  acc.add(fma(wT, __ldg(Kabd + (size_t)j * n), __ldg(Kab + (size_t)j * n)) * Nb[j]);
+                acc.flush();
+              }
+            } else {
+              for (int j0 = s_lo[b]; j0 <= s_hi[b]; j0 += kLossRun) {
+                const int j1 = min(s_hi[b], j0 + kLossRun - 1);
+                for (int j = j0; j <= j1; ++j) acc.add(__ldg(Kab + (size_t)j * n) * Nb[j]);
+                acc.flush();
+              }
             }
           }
           R = dt * sm.M[r] * Num<T>::val(acc.sum());
@@ -636,7 +660,9 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
               const T lj = sm.lam[rj];
               if (lj < li) {
                 const int b = rj / n, j = rj - b * n;
-                const T Kv = __ldg(Kr + (size_t)(s_sp[a] * S + s_sp[b]) * n * n + (size_t)j * n + i);
+                const size_t kidx = (size_t)(s_sp[a] * S + s_sp[b]) * n * n + (size_t)j * n + i;
+                T Kv = __ldg(Kr + kidx);
+                if (lev) Kv = fma(wT, __ldg(Sel<T>::Kr_d(G) + kidx), Kv);
                 acc.add((li - lj) * Kv * sm.N[rj]);
               }
             }
@@ -668,10 +694,17 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
           const int ol = on ? f - kq * O : 0;
           const int k = on ? kq + 1 : 0;
           typename Num<T>::Sum st_, up_;
-          if (limited)
-            gain_task<T, true>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, &st_, &up_);
-          else
-            gain_task<T, false>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, &st_, &up_);
+          if (LEV && lev) {
+            if (limited)
+              gain_task<T, true, LEV>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, wT, &st_, &up_);
+            else
+              gain_task<T, false, LEV>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, wT, &st_, &up_);
+          } else {
+            if (limited)
+              gain_task<T, true, false>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, wT, &st_, &up_);
+            else
+              gain_task<T, false, false>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, wT, &st_, &up_);
+          }
           if (on) {
             sm.stay[ol * n + k] = st_;
             sm.up[ol * n + k] = up_;
@@ -729,17 +762,18 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
   }
 }
 
-template <typename T>
+template <typename T, bool LEV>
 cudaError_t plan_t(const Tables& t, int block_dim, int n_sms, CoalLaunch* out) {
   int nmax = 0;
   for (int g = 0; g < t.G; ++g) nmax = t.g[g].n > nmax ? t.g[g].n : nmax;
   const size_t smem = Smem<T>::bytes(nmax, t.S);
-  cudaError_t e = cudaFuncSetAttribute(k_coal<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto* kern = k_coal<T, LEV>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // Give shared memory what the register-limited number of resident CTAs needs and leave the
   // rest of the SM's 256 KB to L1 (the kernel and math tables are read through it).
   cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, k_coal<T>);
+  e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
   int dev = 0, regs_sm = 0, smem_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -750,10 +784,10 @@ cudaError_t plan_t(const Tables& t, int block_dim, int n_sms, CoalLaunch* out) {
   const int by_regs = std::max(regs_cta > 0 ? regs_sm / regs_cta : 1, 1);
   const size_t need = (size_t)by_regs * (smem + fa.sharedSizeBytes + 1024);
   const int carve = (int)std::min<size_t>(100, (need * 100 + smem_sm - 1) / std::max(smem_sm, 1));
-  if ((e = cudaFuncSetAttribute(k_coal<T>, cudaFuncAttributePreferredSharedMemoryCarveout, carve)) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve)) != cudaSuccess)
     return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coal<T>, block_dim, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block_dim, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   out->block_dim = block_dim;
@@ -823,7 +857,9 @@ size_t coal_smem_bytes(const Tables& t, int precision) {
 
 cudaError_t coal_plan(const Tables& t, int precision, int block_dim, int n_sms, CoalLaunch* out) {
   if (t.mode == 1) return sweep_plan(block_dim, n_sms, out);
-  return precision == 0 ? plan_t<double>(t, block_dim, n_sms, out) : plan_t<float>(t, block_dim, n_sms, out);
+  if (t.levels)
+    return precision == 0 ? plan_t<double, true>(t, block_dim, n_sms, out) : plan_t<float, true>(t, block_dim, n_sms, out);
+  return precision == 0 ? plan_t<double, false>(t, block_dim, n_sms, out) : plan_t<float, false>(t, block_dim, n_sms, out);
 }
 
 cudaError_t launch_coal(const Tables& t, int precision, const PointsDev& p, const Scratch& s, double dt,
@@ -831,12 +867,11 @@ cudaError_t launch_coal(const Tables& t, int precision, const PointsDev& p, cons
   if (t.mode == 1) return launch_sweep(t, p, s, dt, n_steps, plan, stream);
   int nmax = 0;
   for (int g = 0; g < t.G; ++g) nmax = t.g[g].n > nmax ? t.g[g].n : nmax;
-  if (precision == 0)
-    k_coal<double><<<plan.grid_dim, plan.block_dim, plan.smem, stream>>>(t, p, s.active_list, s.counters, dt,
-                                                                         n_steps, nmax);
-  else
-    k_coal<float><<<plan.grid_dim, plan.block_dim, plan.smem, stream>>>(t, p, s.active_list, s.counters, dt,
-                                                                        n_steps, nmax);
+  // all four instantiations share one signature
+  void (*kern)(Tables, PointsDev, const int32_t*, int32_t*, double, int, int) =
+      precision == 0 ? (t.levels ? k_coal<double, true> : k_coal<double, false>)
+                     : (t.levels ? k_coal<float, true> : k_coal<float, false>);
+  kern<<<plan.grid_dim, plan.block_dim, plan.smem, stream>>>(t, p, s.active_list, s.counters, dt, n_steps, nmax);
   return cudaGetLastError();
 }
 

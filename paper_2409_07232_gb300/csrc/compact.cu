@@ -35,6 +35,10 @@ __device__ __forceinline__ int classify_point(const Tables& t, const PointsDev& 
     *st = 2;
     return -1;
   }
+  if (t.levels && pd.pressure && !isfinite(pd.pressure[p])) {  // the kernels need a pressure
+    *st = 2;
+    return -1;
+  }
   const int ns = __popc(mask);
   const int64_t len = pd.offset[p + 1] - pd.offset[p];
   if (len != (int64_t)ns * t.g[g].n) {

@@ -171,6 +171,7 @@ PointsDev to_dev(const fsbm_coal_state* s) {
   p.mass_budget = s->mass_budget;
   p.mass_error = s->mass_error;
   p.status = s->status;
+  p.pressure = s->pressure;
   return p;
 }
 
@@ -298,6 +299,12 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
   if (cfg->mode == 1 && cfg->precision != FSBM_FP64) return bail(FSBM_E_UNSUPPORTED);
   if (!std::isfinite(cfg->t_min_K) || !(cfg->active_rel_threshold >= 0.0) || !(cfg->active_rel_threshold < 1.0))
     return bail(FSBM_E_ARG);
+  if (cfg->kernels_p2 &&
+      (!std::isfinite(cfg->p1_hpa) || !std::isfinite(cfg->p2_hpa) || cfg->p1_hpa == cfg->p2_hpa))
+    return bail(FSBM_E_ARG);
+  c->t.levels = cfg->kernels_p2 ? 1 : 0;
+  c->t.p1 = cfg->p1_hpa;
+  c->t.p2 = cfg->p2_hpa;
   c->S = S;
   c->G = G;
   c->precision = cfg->precision;
@@ -329,9 +336,12 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
     if (n < 2 || n > kMaxBins || !(x0 > 0.0) || !std::isfinite(x0) || !(al > 1.0) || !(al <= 2.0))
       return bail(FSBM_E_ARG);
     const double* Kg = cfg->kernels + koff;
+    const double* K2g = cfg->kernels_p2 ? cfg->kernels_p2 + koff : nullptr;
     const size_t nn = (size_t)n * n;
-    for (size_t e = 0; e < (size_t)npairs * nn; ++e)
+    for (size_t e = 0; e < (size_t)npairs * nn; ++e) {
       if (!(Kg[e] >= 0.0) || !std::isfinite(Kg[e])) return bail(FSBM_E_ARG);
+      if (K2g && (!(K2g[e] >= 0.0) || !std::isfinite(K2g[e]))) return bail(FSBM_E_ARG);
+    }
     koff += (size_t)npairs * nn;
     for (int ns = 1; ns <= S; ++ns)
       cls.push_back(Cls{(double)ns * n * (n + 1) / 2.0 + (double)ns * (ns - 1) / 2.0 * (double)n * n, g, ns});
@@ -352,28 +362,47 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
       gd.d_lo[kap[d]] = std::min(gd.d_lo[kap[d]], d);
       gd.d_hi[kap[d]] = std::max(gd.d_hi[kap[d]], d);
     }
-    std::vector<double> x(n), invx(n), Kd((size_t)S * S * nn, 0.0), Kr((size_t)S * S * nn, 0.0);
+    std::vector<double> x(n), invx(n);
     for (int k = 0; k < n; ++k) {
       x[k] = x0 * std::pow(al, (double)k);
       invx[k] = 1.0 / x[k];
     }
     const int S2 = S * S;
-    for (int s = 0; s < S; ++s)
-      for (int l = 0; l < S; ++l) {
-        double* kr = Kr.data() + (size_t)(s * S + l) * nn;
-        // Kd[d][m][s*S+l]: the orientations of one (d, m) sit side by side. The same-species
-        // diagonal pair (d = 0, s = l) is counted once with weight 1/2 (Sec. II's collection
-        // of a bin with itself), so its entry holds K / 2 and the gain pass needs no weight.
-        for (int d = 0; d < n; ++d)
-          for (int m = d; m < n; ++m)
-            Kd[((size_t)d * n + m) * S2 + (s * S + l)] =
-                kern_entry(Kg, S, n, s, m - d, l, m) * ((d == 0 && s == l) ? 0.5 : 1.0);
-        for (int j = 0; j < n; ++j)
-          for (int i = 0; i < n; ++i) kr[(size_t)j * n + i] = kern_entry(Kg, S, n, s, i, l, j);
-      }
+    // the two layouts of one grid's kernel tables
+    auto layouts = [&](const double* Kt, std::vector<double>& Kd, std::vector<double>& Kr) {
+      Kd.assign((size_t)S2 * nn, 0.0);
+      Kr.assign((size_t)S2 * nn, 0.0);
+      for (int s = 0; s < S; ++s)
+        for (int l = 0; l < S; ++l) {
+          double* kr = Kr.data() + (size_t)(s * S + l) * nn;
+          // Kd[d][m][s*S+l]: the orientations of one (d, m) sit side by side. The same-species
+          // diagonal pair (d = 0, s = l) is counted once with weight 1/2 (a bin collecting
+          // itself), so its entry holds K / 2 and the gain pass needs no weight.
+          for (int d = 0; d < n; ++d)
+            for (int m = d; m < n; ++m)
+              Kd[((size_t)d * n + m) * S2 + (s * S + l)] =
+                  kern_entry(Kt, S, n, s, m - d, l, m) * ((d == 0 && s == l) ? 0.5 : 1.0);
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) kr[(size_t)j * n + i] = kern_entry(Kt, S, n, s, i, l, j);
+        }
+    };
+    std::vector<double> Kd, Kr;
+    layouts(Kg, Kd, Kr);
     std::vector<float> x32(x.begin(), x.end()), invx32(invx.begin(), invx.end()), cd32(cd.begin(), cd.end()),
         Kd32(Kd.begin(), Kd.end()), Kr32(Kr.begin(), Kr.end());
     fsbm_status st;
+    if (K2g) {
+      // second pressure level: the differences D = K2 - K1 in both layouts and precisions
+      std::vector<double> Kd2, Kr2;
+      layouts(K2g, Kd2, Kr2);
+      for (size_t e = 0; e < Kd2.size(); ++e) Kd2[e] -= Kd[e];
+      for (size_t e = 0; e < Kr2.size(); ++e) Kr2[e] -= Kr[e];
+      std::vector<float> Kd2f(Kd2.begin(), Kd2.end()), Kr2f(Kr2.begin(), Kr2.end());
+      if ((st = upload(c, Kd2, &gd.Kd64_d)) != FSBM_OK || (st = upload(c, Kd2f, &gd.Kd32_d)) != FSBM_OK ||
+          (st = upload(c, Kr2, &gd.Kr64_d)) != FSBM_OK || (st = upload(c, Kr2f, &gd.Kr32_d)) != FSBM_OK ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return bail(st != FSBM_OK ? st : FSBM_E_CUDA);
+    }
     if ((st = upload(c, x, &gd.x64)) != FSBM_OK || (st = upload(c, x32, &gd.x32)) != FSBM_OK ||
         (st = upload(c, invx, &gd.invx64)) != FSBM_OK || (st = upload(c, invx32, &gd.invx32)) != FSBM_OK ||
         (st = upload(c, cd, &gd.cd64)) != FSBM_OK || (st = upload(c, cd32, &gd.cd32)) != FSBM_OK ||
@@ -454,8 +483,8 @@ fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int6
   const size_t spec_bytes = (size_t)total * esz;
   // device mirror of the metadata and outputs: offsets, outputs, then byte arrays
   const size_t n = (size_t)n_points;
-  const size_t meta = sizeof(int64_t) * (n + 1) + sizeof(double) * 2 * n + sizeof(int32_t) * n + sizeof(float) * n +
-                      3 * n + 64;
+  const size_t meta = sizeof(int64_t) * (n + 1) + sizeof(double) * 2 * n + sizeof(int32_t) * n +
+                      2 * sizeof(float) * n + 3 * n + 64;
   if (spec_bytes > c->h_spectra_bytes) {
     if (c->h_spectra) cudaFree(c->h_spectra);
     c->h_spectra = nullptr;
@@ -481,6 +510,8 @@ fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int6
   m += sizeof(int32_t) * n;
   float* d_T = reinterpret_cast<float*>(m);
   m += sizeof(float) * n;
+  float* d_P = reinterpret_cast<float*>(m);
+  m += sizeof(float) * n;
   uint8_t* d_gid = reinterpret_cast<uint8_t*>(m);
   uint8_t* d_mask = d_gid + n;
   uint8_t* d_cl = d_mask + n;
@@ -493,6 +524,8 @@ fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int6
   CU(c, cudaMemcpyAsync(d_mask, h->species_mask, n, cudaMemcpyHostToDevice, sm));
   if (h->cloudy) CU(c, cudaMemcpyAsync(d_cl, h->cloudy, n, cudaMemcpyHostToDevice, sm));
   if (h->temperature) CU(c, cudaMemcpyAsync(d_T, h->temperature, sizeof(float) * n, cudaMemcpyHostToDevice, sm));
+  const bool has_p = h->pressure && c->t.levels;
+  if (has_p) CU(c, cudaMemcpyAsync(d_P, h->pressure, sizeof(float) * n, cudaMemcpyHostToDevice, sm));
   PointsDev p;
   p.spectra = d_spec - (size_t)base * esz;  // the offsets index from the caller's base
   p.offset = d_off;
@@ -503,6 +536,7 @@ fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int6
   p.mass_budget = d_bud;
   p.mass_error = d_err;
   p.status = d_st;
+  p.pressure = has_p ? d_P : nullptr;
   st = run_step(c, p, n_points, dt, n_steps);
   if (st != FSBM_OK) return st;
   CU(c, cudaMemcpyAsync(static_cast<char*>(h->spectra) + (size_t)base * esz, d_spec, spec_bytes,

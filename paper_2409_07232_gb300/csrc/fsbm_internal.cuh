@@ -49,12 +49,20 @@ struct GridDev {
   const float* Kd32;
   const double* Kr64;
   const float* Kr32;
+  // second pressure level: D = K2 - K1 in both layouts (NULL without a second level);
+  // a point with weight w reads K1 + w D
+  const double* Kd64_d;
+  const float* Kd32_d;
+  const double* Kr64_d;
+  const float* Kr32_d;
 };
 
 struct Tables {
   int S;
   int G;
   int mode;                       // 0 pairwise (Jacobi), 1 SWEEP (Bott's in-place order, FP64)
+  int levels;                     // 1: kernels at two pressure levels (per-point weight)
+  double p1, p2;                  // their pressures, hPa
   double t_min;
   double tau;
   int8_t product[kMaxSpecies * kMaxSpecies];
@@ -74,7 +82,16 @@ struct PointsDev {
   double* mass_budget;
   double* mass_error;
   int32_t* status;
+  const float* pressure;
 };
+
+// Weight of the second pressure level at pressure p: (p1 - p) / (p1 - p2) clamped to [0, 1];
+// 0 without levels or pressures. Callers have rejected non-finite pressures.
+__device__ __forceinline__ double level_weight(const Tables& t, const PointsDev& pd, int p) {
+  if (!t.levels || !pd.pressure) return 0.0;
+  const double w = (t.p1 - (double)pd.pressure[p]) / (t.p1 - t.p2);
+  return fmin(fmax(w, 0.0), 1.0);
+}
 
 // Context-owned scratch of one step.
 struct Scratch {

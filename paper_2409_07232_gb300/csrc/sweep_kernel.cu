@@ -94,6 +94,9 @@ __global__ void k_sweep(Tables t, PointsDev pd, const int32_t* __restrict__ list
     const double* __restrict__ Kr = G.Kr64;
     const double* __restrict__ cd = G.cd64;
     const int* __restrict__ kapd = G.kapd;
+    // kernels at two pressure levels: K1 + w (K2 - K1) (w = 0: the first table alone)
+    const double wlev = level_weight(t, pd, p);
+    const double* __restrict__ Krd = wlev != 0.0 ? G.Kr64_d : nullptr;
     int status = 0;
     double emax = 0.0;
     for (int step = 0; step < n_steps; ++step) {
@@ -128,7 +131,8 @@ __global__ void k_sweep(Tables t, PointsDev pd, const int32_t* __restrict__ list
               const double Ni = Ma[i] / xi, Nj = Mb[j] / xj;
               const int dd = i < j ? j - i : i - j;
               const int k = (i > j ? i : j) + kapd[dd];
-              const double K = __ldg(Kab + (size_t)j * n + i);
+              double K = __ldg(Kab + (size_t)j * n + i);
+              if (Krd) K = K + wlev * __ldg(Krd + (size_t)(sp[sa] * S + sp[sb]) * n * n + (size_t)j * n + i);
               double C;
               int emptied = 0;  // the bin whose cap decided C (1: i, 2: j) ends at exactly 0
               const bool diag = sa == sb && i == j;

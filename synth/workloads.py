@@ -22,6 +22,7 @@ Units are CGS (g, cm, s). Seeds are (config index) * 1000 + 1.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass, field
 from typing import Optional, Sequence
@@ -438,9 +439,7 @@ def with_pressure_levels(w: Workload, seed: int = 17, p_levels=(750.0, 500.0), p
     rng = np.random.default_rng(seed)
     f = math.sqrt(p_levels[0] / p_levels[1])
     k2 = w.kernels * f * rng.uniform(0.9, 1.1, size=w.kernels.shape)
-    out = subset(w, np.arange(w.n_points))
-    out.name = w.name + "+p"
-    out.kernels_p2 = k2.astype(np.float64)
-    out.p_levels = (float(p_levels[0]), float(p_levels[1]))
-    out.pressure = rng.uniform(p_range[0], p_range[1], size=w.n_points).astype(np.float32)
-    return out
+    # the spectra and metadata arrays are shared with ``w`` (state() copies the spectra)
+    return dataclasses.replace(
+        w, name=w.name + "+p", kernels_p2=k2.astype(np.float64), p_levels=(float(p_levels[0]), float(p_levels[1])),
+        pressure=rng.uniform(p_range[0], p_range[1], size=w.n_points).astype(np.float32), meta=dict(w.meta))
