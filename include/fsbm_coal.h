@@ -192,6 +192,41 @@ FSBM_API fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* ctx, const fsbm_coal_sta
 FSBM_API fsbm_status fsbm_coal_step_noalloc(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points,
                                             double dt, int32_t n_steps);
 
+/* Bin fields in WRF's own memory layout (Sec. I: a patch's arrays span the memory ranges
+ * ims:ime, kms:kme, jms:jme, and a thread works on a tile its:ite, kts:kte, jts:jte inside
+ * them; Sec. III, Listing 1: the collision step runs at every tile point (i, k, j) warmer than
+ * t_min_K; Sec. V-B, Listing 5: a predicate array kept from the loop fission says where the
+ * collision step is called). Ranges are inclusive, in the caller's index space (Fortran's
+ * 1-based indices work as they are). All pointers are device pointers, caller-owned.        */
+typedef struct {
+  void* ff[5];                  /* per species id a: its bins, element (i, k, j, bin b) at
+                                   ((b * jm + (j - jms)) * km + (k - kms)) * im + (i - ims),
+                                   im = ime - ims + 1 and so on (i fastest: Fortran's
+                                   ff(i, k, j, b)); double or float as the context's
+                                   precision; NULL = species not carried. Updated in place at
+                                   the points the step runs on, untouched elsewhere.           */
+  const float* temperature;     /* [j][k][i] over the memory ranges, K; NULL = all warm       */
+  const uint8_t* predicate;     /* [j][k][i], nonzero = run the collision step here;
+                                   NULL = everywhere (still subject to temperature)           */
+  const float* pressure;        /* [j][k][i] hPa for kernels at two pressure levels, or NULL */
+  int32_t* status;              /* [j][k][i] out (FSBM_ST_* bits) at tile points, or NULL   */
+  double* mass_budget;          /* [j][k][i] out at tile points, or NULL                    */
+  double* mass_error;           /* [j][k][i] out at tile points, or NULL                    */
+  int32_t ims, ime, kms, kme, jms, jme;  /* memory ranges                                   */
+  int32_t its, ite, kts, kte, jts, jte;  /* tile ranges, inside the memory ranges; an empty
+                                            tile (its > ite, ...) is a no-op                 */
+  int32_t grid;                 /* bin grid (index into bins_per_grid) of every point         */
+} fsbm_wrf_state;
+
+/* Advance every tile point of a WRF-layout state n_steps collision steps of dt seconds: the
+ * tile's points are packed into a context-owned buffer of the packed layout, stepped exactly
+ * as by fsbm_coal_step, and the points it ran on are written back. Asynchronous on the
+ * context's stream. The buffer holds (tile points) x (species carried) x bins values of the
+ * context's precision and grows on demand (about 8.4 GB for a 425 x 300 x 50 tile with 5
+ * species, 33 bins in FP64). Errors: FSBM_E_ARG for ranges outside the memory ranges, an
+ * unknown grid or no species; FSBM_E_OOM if the buffer cannot be allocated. */
+FSBM_API fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* ctx, const fsbm_wrf_state* state, double dt, int32_t n_steps);
+
 /* Time the collision kernel for each candidate CTA size (128, 256, 512 threads) on a copy of
  * the first 2^18 points of the given device state (all of it if smaller), three collision
  * steps of 5 s each, and keep the fastest for later steps. The caller's spectra are not

@@ -121,6 +121,15 @@ class FsbmCoal:
         fsbm_coal_step_host(self.ctx, st, n, dt, n_steps)
         return out
 
+    def step_wrf(self, ff, mem, tile, dt: float, n_steps: int, grid: int = 0, temperature=None, predicate=None,
+                 pressure=None, status=None, mass_budget=None, mass_error=None) -> None:
+        """fsbm_coal_step_wrf on device tensors in WRF's layout: ``ff`` holds one tensor (or None)
+        per species id, each [bins][j][k][i] over the memory ranges ``mem`` = (ims, ime, kms,
+        kme, jms, jme); ``tile`` = (its, ite, kts, kte, jts, jte). Fields are updated in place."""
+        st = binding.make_wrf_state(ff, mem, tile, grid, temperature, predicate, pressure, status, mass_budget,
+                                    mass_error)
+        binding.fsbm_coal_step_wrf(self.ctx, st, dt, n_steps)
+
     def autotune(self, ds: DeviceState) -> None:
         fsbm_coal_autotune(self.ctx, ds.struct, ds.n_points)
 

@@ -37,7 +37,8 @@ _STATUS_NAMES = {0: "FSBM_OK", -1: "FSBM_E_ARG", -2: "FSBM_E_CUDA", -3: "FSBM_E_
                  -4: "FSBM_E_TIMEOUT", -5: "FSBM_E_UNSUPPORTED"}
 
 # Every entry point include/fsbm_coal.h declares.
-EXPORTS = ("fsbm_coal_init", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_step_noalloc", "fsbm_coal_autotune",
+EXPORTS = ("fsbm_coal_init", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_step_noalloc", "fsbm_coal_step_wrf",
+           "fsbm_coal_autotune",
            "fsbm_coal_set_graph", "fsbm_coal_set_block", "fsbm_coal_set_timing", "fsbm_coal_get_stats",
            "fsbm_coal_get_active_list", "fsbm_coal_math_check", "fsbm_coal_destroy", "fsbm_coal_last_error")
 
@@ -82,6 +83,23 @@ class fsbm_coal_state(ctypes.Structure):
     ]
 
 
+class fsbm_wrf_state(ctypes.Structure):
+    _fields_ = [
+        ("ff", ctypes.c_void_p * 5),
+        ("temperature", ctypes.c_void_p),
+        ("predicate", ctypes.c_void_p),
+        ("pressure", ctypes.c_void_p),
+        ("status", ctypes.c_void_p),
+        ("mass_budget", ctypes.c_void_p),
+        ("mass_error", ctypes.c_void_p),
+        ("ims", ctypes.c_int32), ("ime", ctypes.c_int32), ("kms", ctypes.c_int32), ("kme", ctypes.c_int32),
+        ("jms", ctypes.c_int32), ("jme", ctypes.c_int32),
+        ("its", ctypes.c_int32), ("ite", ctypes.c_int32), ("kts", ctypes.c_int32), ("kte", ctypes.c_int32),
+        ("jts", ctypes.c_int32), ("jte", ctypes.c_int32),
+        ("grid", ctypes.c_int32),
+    ]
+
+
 class fsbm_coal_stats(ctypes.Structure):
     _fields_ = [
         ("n_points", ctypes.c_int64),
@@ -119,6 +137,7 @@ def load(path: str = LIB_PATH):
                                     ctypes.c_int),
             "fsbm_coal_step_noalloc": ([V, P(fsbm_coal_state), ctypes.c_int64, ctypes.c_double, ctypes.c_int32],
                                        ctypes.c_int),
+            "fsbm_coal_step_wrf": ([V, P(fsbm_wrf_state), ctypes.c_double, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_autotune": ([V, P(fsbm_coal_state), ctypes.c_int64], ctypes.c_int),
             "fsbm_coal_set_graph": ([V, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_set_block": ([V, ctypes.c_int32], ctypes.c_int),
@@ -201,6 +220,20 @@ def fsbm_coal_step_noalloc(ctx, state: fsbm_coal_state, n_points: int, dt: float
     allocation; at most 262144 points per call)."""
     _check(ctx, load().fsbm_coal_step_noalloc(ctx, ctypes.byref(state), int(n_points), float(dt), int(n_steps)),
            "fsbm_coal_step_noalloc")
+
+
+def make_wrf_state(ff, mem, tile, grid=0, temperature=None, predicate=None, pressure=None, status=None,
+                   mass_budget=None, mass_error=None) -> fsbm_wrf_state:
+    """Build an fsbm_wrf_state. ``ff``: five device tensors or None (by species id);
+    ``mem``/``tile``: (ims, ime, kms, kme, jms, jme) and (its, ite, kts, kte, jts, jte)."""
+    ffp = (ctypes.c_void_p * 5)(*[_ptr(f) for f in list(ff) + [None] * (5 - len(ff))])
+    return fsbm_wrf_state(ffp, _ptr(temperature), _ptr(predicate), _ptr(pressure), _ptr(status),
+                          _ptr(mass_budget), _ptr(mass_error), *[int(v) for v in mem], *[int(v) for v in tile],
+                          int(grid))
+
+
+def fsbm_coal_step_wrf(ctx, state: fsbm_wrf_state, dt: float, n_steps: int) -> None:
+    _check(ctx, load().fsbm_coal_step_wrf(ctx, ctypes.byref(state), float(dt), int(n_steps)), "fsbm_coal_step_wrf")
 
 
 def fsbm_coal_autotune(ctx, state: fsbm_coal_state, n_points: int) -> None:

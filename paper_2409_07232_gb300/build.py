@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsbm_coal.so")
 HEADER = os.path.join(ROOT, "include", "fsbm_coal.h")
-SOURCES = ["compact.cu", "coal_kernel.cu", "sweep_kernel.cu", "fsbm_coal.cu"]
+SOURCES = ["compact.cu", "coal_kernel.cu", "sweep_kernel.cu", "wrf_frontend.cu", "fsbm_coal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 # The SWEEP kernel rounds every product and sum separately, as the C oracle does: its in-place

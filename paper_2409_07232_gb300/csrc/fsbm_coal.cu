@@ -33,6 +33,11 @@ struct fsbm_coal_ctx {
   size_t h_spectra_bytes = 0;
   void* h_meta = nullptr;
   size_t h_meta_bytes = 0;
+  // packed copy of a WRF-layout tile for fsbm_coal_step_wrf
+  void* wrf_spec = nullptr;
+  size_t wrf_spec_bytes = 0;
+  void* wrf_meta = nullptr;
+  size_t wrf_meta_bytes = 0;
   // launch plan
   int block_dim = 256;
   CoalLaunch plan{};
@@ -548,6 +553,106 @@ fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int6
   return FSBM_OK;
 }
 
+fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* c, const fsbm_wrf_state* w, double dt, int32_t n_steps) {
+  if (!c) return FSBM_E_ARG;
+  if (!w) return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: state is NULL");
+  if (!(dt >= 0.0) || !std::isfinite(dt) || n_steps < 0)
+    return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: dt must be finite and >= 0, n_steps >= 0");
+  if (w->grid < 0 || w->grid >= c->G) return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: unknown grid");
+  if (w->ime < w->ims || w->kme < w->kms || w->jme < w->jms)
+    return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: empty memory ranges");
+  const int64_t ti = (int64_t)w->ite - w->its + 1, tk = (int64_t)w->kte - w->kts + 1, tj = (int64_t)w->jte - w->jts + 1;
+  if (ti <= 0 || tk <= 0 || tj <= 0) return FSBM_OK;  // empty tile
+  if (w->its < w->ims || w->ite > w->ime || w->kts < w->kms || w->kte > w->kme || w->jts < w->jms || w->jte > w->jme)
+    return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: tile ranges outside the memory ranges");
+  WrfDev d{};
+  d.ns = 0;
+  d.mask = 0;
+  for (int a = 0; a < c->S; ++a)
+    if (w->ff[a]) {
+      d.ff[d.ns++] = w->ff[a];
+      d.mask |= 1u << a;
+    }
+  for (int a = c->S; a < kMaxSpecies; ++a)
+    if (w->ff[a]) return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: a field for a species beyond n_species");
+  if (d.ns == 0) return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: no species field");
+  d.n = c->t.g[w->grid].n;
+  d.grid = w->grid;
+  d.temperature = w->temperature;
+  d.predicate = w->predicate;
+  d.pressure = w->pressure;
+  d.status = w->status;
+  d.mass_budget = w->mass_budget;
+  d.mass_error = w->mass_error;
+  d.ims = w->ims;
+  d.kms = w->kms;
+  d.jms = w->jms;
+  d.im = w->ime - w->ims + 1;
+  d.km = w->kme - w->kms + 1;
+  d.jm = w->jme - w->jms + 1;
+  d.its = w->its;
+  d.kts = w->kts;
+  d.jts = w->jts;
+  d.ti = (int)ti;
+  d.tk = (int)tk;
+  d.tj = (int)tj;
+  const int64_t n_tile = ti * tk * tj;
+  if (n_tile > INT32_MAX - 1) return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: more than 2^31 - 2 tile points");
+  const size_t esz = c->precision == FSBM_FP64 ? sizeof(double) : sizeof(float);
+  const size_t n = (size_t)n_tile;
+  const size_t spec_bytes = n * (size_t)d.ns * d.n * esz;
+  const size_t meta = sizeof(int64_t) * (n + 1) + sizeof(double) * 2 * n + sizeof(int32_t) * n +
+                      2 * sizeof(float) * n + 3 * n + 64;
+  if (spec_bytes > c->wrf_spec_bytes) {
+    if (c->wrf_spec) cudaFree(c->wrf_spec);
+    c->wrf_spec = nullptr;
+    c->wrf_spec_bytes = 0;
+    if (cudaMalloc(&c->wrf_spec, spec_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->wrf_spec = nullptr;
+      return fail(c, FSBM_E_OOM, "fsbm_coal_step_wrf: packed tile buffer");
+    }
+    c->wrf_spec_bytes = spec_bytes;
+  }
+  if (meta > c->wrf_meta_bytes) {
+    if (c->wrf_meta) cudaFree(c->wrf_meta);
+    c->wrf_meta = nullptr;
+    c->wrf_meta_bytes = 0;
+    if (cudaMalloc(&c->wrf_meta, meta) != cudaSuccess) {
+      cudaGetLastError();
+      c->wrf_meta = nullptr;
+      return fail(c, FSBM_E_OOM, "fsbm_coal_step_wrf: packed tile metadata");
+    }
+    c->wrf_meta_bytes = meta;
+  }
+  char* m = static_cast<char*>(c->wrf_meta);
+  PointsDev p{};
+  p.offset = reinterpret_cast<int64_t*>(m);
+  m += sizeof(int64_t) * (n + 1);
+  p.mass_budget = reinterpret_cast<double*>(m);
+  m += sizeof(double) * n;
+  p.mass_error = reinterpret_cast<double*>(m);
+  m += sizeof(double) * n;
+  p.status = reinterpret_cast<int32_t*>(m);
+  m += sizeof(int32_t) * n;
+  float* tbuf = reinterpret_cast<float*>(m);
+  m += sizeof(float) * n;
+  float* pbuf = reinterpret_cast<float*>(m);
+  m += sizeof(float) * n;
+  p.grid_id = reinterpret_cast<uint8_t*>(m);
+  p.species_mask = reinterpret_cast<uint8_t*>(m) + n;
+  p.cloudy = reinterpret_cast<uint8_t*>(m) + 2 * n;
+  p.temperature = w->temperature ? tbuf : nullptr;
+  p.pressure = (w->pressure && c->t.levels) ? pbuf : nullptr;
+  p.spectra = c->wrf_spec;
+  d.pressure = p.pressure ? w->pressure : nullptr;
+  CU(c, launch_wrf_pack(d, c->precision, p, n_tile, c->t.t_min, c->stream));
+  fsbm_status st = run_step(c, p, n_tile, dt, n_steps);
+  if (st != FSBM_OK) return st;
+  CU(c, launch_wrf_unpack(d, c->precision, p, n_tile, c->stream));
+  return FSBM_OK;
+}
+
 fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points) {
   if (!c) return FSBM_E_ARG;
   fsbm_status st = check_state(c, s, n_points, 1.0, 1);
@@ -696,6 +801,8 @@ fsbm_status fsbm_coal_destroy(fsbm_coal_ctx* c) {
   if (c->scratch.counters) cudaFree(c->scratch.counters);
   if (c->h_spectra) cudaFree(c->h_spectra);
   if (c->h_meta) cudaFree(c->h_meta);
+  if (c->wrf_spec) cudaFree(c->wrf_spec);
+  if (c->wrf_meta) cudaFree(c->wrf_meta);
   for (auto& ev : c->ev_coal) c->ev_pool.insert(c->ev_pool.end(), {ev.first, ev.second});
   for (auto& ev : c->ev_step) c->ev_pool.insert(c->ev_pool.end(), {ev.first, ev.second});
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);

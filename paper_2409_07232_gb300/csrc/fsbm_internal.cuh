@@ -117,6 +117,29 @@ size_t coal_smem_bytes(const Tables& t, int precision);  // dynamic shared memor
 cudaError_t coal_plan(const Tables& t, int precision, int block_dim, int n_sms, CoalLaunch* out);
 cudaError_t launch_coal(const Tables& t, int precision, const PointsDev& p, const Scratch& s, double dt,
                         int n_steps, const CoalLaunch& plan, cudaStream_t stream);
+// WRF-layout fields (the public fsbm_wrf_state, resolved): memory extents, tile extents and the
+// carried species in slot order.
+struct WrfDev {
+  const void* ff[kMaxSpecies];  // by slot (species id sp[s])
+  int ns;
+  int n;                        // bins of the grid
+  int grid;
+  unsigned mask;                // species mask of every point
+  const float* temperature;
+  const uint8_t* predicate;
+  const float* pressure;
+  int32_t* status;
+  double* mass_budget;
+  double* mass_error;
+  int ims, kms, jms, im, km, jm;  // memory origin and extents
+  int its, kts, jts, ti, tk, tj;  // tile origin and extents
+};
+// wrf_frontend.cu: tile -> packed points (metadata and spectra), and back
+cudaError_t launch_wrf_pack(const WrfDev& w, int precision, const PointsDev& pk, int64_t n_tile, double t_min,
+                            cudaStream_t stream);
+cudaError_t launch_wrf_unpack(const WrfDev& w, int precision, const PointsDev& pk, int64_t n_tile,
+                              cudaStream_t stream);
+
 // sweep_kernel.cu: the SWEEP form, one thread per point (launched by launch_coal when mode = 1)
 cudaError_t sweep_plan(int block_dim, int n_sms, CoalLaunch* out);
 cudaError_t launch_sweep(const Tables& t, const PointsDev& p, const Scratch& s, double dt, int n_steps,
