@@ -269,6 +269,45 @@ def run_form(pkg, torch, w, precision, steps, warmup, graph=False, mode=0):
     return out
 
 
+def run_wrf_form(pkg, torch, w, precision, steps, warmup):
+    """The CONUS-shaped domain laid out in WRF's arrays (one [bin][j][k][i] array per species,
+    the cloud mask as the predicate; memory point m holds the domain's point m), stepped through
+    fsbm_coal_step_wrf: pack, compaction, collision kernel, unpack. Returns value and time."""
+    S, n = w.n_species, w.bins_per_grid[0]
+    nx, ny, nz = w.meta.get("shape", (w.n_points, 1, 1))
+    im, km, jm = nx, nz, ny
+    assert im * km * jm == w.n_points
+    dtype = torch.float64 if precision == pkg.FSBM_FP64 else torch.float32
+    act = np.nonzero(w.species_mask)[0]
+    with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
+        dev = fc.device
+        spec = torch.from_numpy(w.spectra).to(dev, dtype).view(-1, S, n)  # cloudy points, all species
+        ff = []
+        for a in range(S):
+            f = torch.zeros((n, w.n_points), dtype=dtype, device=dev)
+            f[:, torch.from_numpy(act).to(dev)] = spec[:, a, :].t()
+            ff.append(f.contiguous())
+        pred = torch.from_numpy(w.cloudy).to(dev)
+        temp = torch.from_numpy(w.temperature).to(dev)
+        st = torch.zeros(w.n_points, dtype=torch.int32, device=dev)
+        mem = (1, im, 1, km, 1, jm)
+        fc.set_timing(False)
+        for _ in range(warmup):
+            fc.step_wrf(ff, mem, mem, w.dt, w.n_steps, temperature=temp, predicate=pred, status=st)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(fc.stream)
+        for _ in range(steps):
+            fc.step_wrf(ff, mem, mem, w.dt, w.n_steps, temperature=temp, predicate=pred, status=st)
+        e1.record(fc.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        n_active = int(((st == 0) | (st == 1)).sum().item())
+    return dict(value=n_active * w.n_steps * steps / (ms / 1e3), ms_per_step=ms / steps, n_active=n_active,
+                points=w.n_points, layout="[species][bin][j][k][i], i fastest; tile = whole domain")
+
+
 def pairs_per_active(w):
     """Bin pairs per collision step summed over the active points (every bin active)."""
     act = (w.species_mask > 0)
@@ -417,6 +456,8 @@ def main():
         rlv32 = run_form(pkg, torch, lv32, pkg.FSBM_FP32_SPLIT, 2, 3, graph=True)
         lv64 = synth.with_pressure_levels(synth.conus_sample(50_000, 0, seed=10), seed=11)
         rlv64 = run_form(pkg, torch, lv64, pkg.FSBM_FP64, 1, 3)
+        if int(np.prod(w.meta.get("shape", (0,)))) == w.n_points:  # the whole domain, not a sample
+            forms["conus_33bin_fp32_split_wrf_layout"] = run_wrf_form(pkg, torch, w, pkg.FSBM_FP32_SPLIT, 2, 3)
         for key, rr, ww, pr in (("stress_264bin_fp32_split_graph", r32, st32, 1),
                                 ("stress_264bin_fp64", r64, st64, 0),
                                 ("ragged_33to264bin_fp32_split_graph", rrag, rag, 1),
