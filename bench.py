@@ -308,6 +308,103 @@ def run_wrf_form(pkg, torch, w, precision, steps, warmup):
                 points=w.n_points, layout="[species][bin][j][k][i], i fastest; tile = whole domain")
 
 
+def _replica_child(rank, R, args_d, barrier, q):
+    """One host process of the replica measurement: its own context and stream on the shared
+    GPU, its own slab of the domain, the same collision calls as the batched run."""
+    import torch
+    import paper_2409_07232_gb300 as pkg
+    w = replica_workload(args_d, rank, R)
+    precision = pkg.FSBM_FP64 if args_d["precision"] == "fp64" else pkg.FSBM_FP32_SPLIT
+    with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
+        ds = fc.upload(w.state(copy=False))
+        fc.set_block(256)
+        for _ in range(args_d["warmup"]):
+            fc.step(ds, w.dt, w.n_steps)
+        torch.cuda.synchronize()
+        barrier.wait()
+        t0 = time.perf_counter()
+        for _ in range(args_d["steps"]):
+            fc.step(ds, w.dt, w.n_steps)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        st = fc.stats()
+        barrier.wait()
+    q.put((rank, t0, t1, int(st["n_active"]) * w.n_steps))
+
+
+def replica_workload(args_d, rank, R):
+    """Slab ``rank`` of R of the bench domain (contiguous along the first horizontal axis, the
+    way an MPI patch decomposition splits it), or the whole domain for R = 1."""
+    import synth
+    w = build_workload("conus", 0, args_d["points"])
+    if R == 1:
+        return w
+    edges = np.linspace(0, w.n_points, R + 1).astype(np.int64)
+    return synth.subset(w, np.arange(edges[rank], edges[rank + 1]))
+
+
+def main_replicas(args):
+    """Throughput of R contexts sharing the GPU against one batched context on the same domain.
+
+    mode "streams": one host process, R contexts on R CUDA streams, calls issued back to back.
+    mode "processes": R host processes (the paper's several MPI ranks per GPU, Sec. VI-A),
+    each with its own CUDA context; without MPS the GPU time-slices between them."""
+    import multiprocessing as mp
+    import torch
+    import paper_2409_07232_gb300 as pkg
+    R = args.replicas
+    args_d = dict(points=args.points, precision=args.precision, steps=args.steps, warmup=args.warmup)
+    precision = pkg.FSBM_FP64 if args.precision == "fp64" else pkg.FSBM_FP32_SPLIT
+
+    def batched_or_streams(nrep):
+        ws = [replica_workload(args_d, r, nrep) for r in range(nrep)]
+        fcs = [pkg.FsbmCoal(w.cfg(), precision=precision, stream=torch.cuda.Stream()) for w in ws]
+        dss = [fc.upload(w.state(copy=False)) for fc, w in zip(fcs, ws)]
+        for fc in fcs:
+            fc.set_block(256)
+        for _ in range(args.warmup):
+            for fc, ds, w in zip(fcs, dss, ws):
+                fc.step(ds, w.dt, w.n_steps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for fc, ds, w in zip(fcs, dss, ws):
+                fc.step(ds, w.dt, w.n_steps)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        act = sum(int(fc.stats()["n_active"]) for fc in fcs)
+        for fc in fcs:
+            fc.close()
+        return act * ws[0].n_steps * args.steps / (t1 - t0), t1 - t0
+
+    single, t_single = batched_or_streams(1)
+    if args.replica_mode == "streams":
+        value, t_rep = batched_or_streams(R)
+    else:
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(R)
+        q = ctx.Queue()
+        procs = [ctx.Process(target=_replica_child, args=(r, R, args_d, barrier, q)) for r in range(R)]
+        for pr in procs:
+            pr.start()
+        res = [q.get(timeout=3600) for _ in range(R)]
+        for pr in procs:
+            pr.join(timeout=600)
+        t_rep = max(r[2] for r in res) - min(r[1] for r in res)
+        value = sum(r[3] for r in res) * args.steps / t_rep
+    line = {
+        "metric": "grid-point coal updates/s with several contexts sharing one GPU",
+        "value": value, "unit": "grid-point coal updates/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "dtype": "f64" if precision == 0 else "f32",
+        "data": "synthetic CONUS-shaped domain split into slabs",
+        "config": {"replicas": R, "mode": args.replica_mode, "points": args.points or "whole domain",
+                   "timing": "host wall clock around all replicas' calls (synchronized start)"},
+        "single_batched": {"value": single, "seconds": t_single},
+        "ratio_to_single_batched": value / single,
+    }
+    print(json.dumps(line))
+
+
 def pairs_per_active(w):
     """Bin pairs per collision step summed over the active points (every bin active)."""
     act = (w.species_mask > 0)
@@ -326,6 +423,10 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32 and 264-bin side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--replicas", type=int, default=1,
+                    help="with R > 1: R contexts share the GPU, each on a slab of the domain; prints their "
+                         "aggregate rate beside one batched context (not the default bench line)")
+    ap.add_argument("--replica-mode", choices=["streams", "processes"], default="processes")
     ap.add_argument("--points", type=int, default=0,
                     help="CONUS workload: a seeded sample of this many cloudy points (plus a quarter as many "
                          "clear ones) instead of the whole domain; for profiling runs")
@@ -339,6 +440,8 @@ def main():
 
     if args.impl == "reference":
         return reference_arm(args, world, rank)
+    if args.replicas > 1:
+        return main_replicas(args)
 
     import torch
     import paper_2409_07232_gb300 as pkg
