@@ -673,26 +673,39 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
         }
       }
 
-      // 4. gains. Lanes run over the flattened list of (target bin 1..n-1, orientation)
+      // 4. gains. Lanes run over the flattened list of (target bin 1..n-2, orientation)
       //    items, orientation fastest: a warp covers about 32/O consecutive targets, whose
       //    distance ranges differ by a few steps at most, so nearly every lane stays busy,
-      //    and the lanes of one (d, m) read one contiguous run of Kd. Warp tasks go out in
-      //    serpentine order, which balances the per-target cost growing with k.
+      //    and the lanes of one (d, m) read one contiguous run of Kd. The top bin's items
+      //    (the most pairs, but no flux) get warp tasks of their own, so that no warp runs
+      //    its flux for a few lanes while the rest walk the top bin; the list is padded at
+      //    its cheap end (low k), where a partly filled warp costs least. Warps claim the
+      //    top tasks first, then the others costliest first (the cost grows with k).
       {
-        const int n_items = (n - 1) * O;
-        const int n_tasks = (n_items + 31) >> 5;
+        const int n_reg = (n - 2) * O;
+        const int n_reg_tasks = (n_reg + 31) >> 5;
+        const int pad = n_reg_tasks * 32 - n_reg;
+        const int n_top_tasks = (O + 31) >> 5;
+        const int n_tasks = n_top_tasks + n_reg_tasks;
         for (;;) {
-          // warps claim tasks costliest first (the cost grows with the target bin)
           int q = 0;
           if (lane == 0) q = atomicAdd(&s_task, 1);
           q = __shfl_sync(0xffffffffu, q, 0);
           if (q >= n_tasks) break;
-          q = n_tasks - 1 - q;
-          const int f = q * 32 + lane;
-          const bool on = f < n_items;
-          const int kq = on ? f / O : 0;
-          const int ol = on ? f - kq * O : 0;
-          const int k = on ? kq + 1 : 0;
+          bool on;
+          int ol, k;
+          if (q < n_top_tasks) {
+            ol = q * 32 + lane;
+            on = ol < O;
+            ol = on ? ol : 0;
+            k = on ? n - 1 : 0;
+          } else {
+            const int f = (n_reg_tasks - 1 - (q - n_top_tasks)) * 32 + lane - pad;
+            on = f >= 0;
+            const int kq = on ? f / O : 0;
+            ol = on ? f - kq * O : 0;
+            k = on ? kq + 1 : 0;
+          }
           typename Num<T>::Sum st_, up_;
           if (LEV && lev) {
             if (limited)
