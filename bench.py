@@ -405,6 +405,44 @@ def main_replicas(args):
     print(json.dumps(line))
 
 
+def main_table(args):
+    """One JSON line per row of the configuration table (configs 1-5 of the workload list):
+    rate, pair rate, ALU roofline fraction and the largest per-step mass error of one call,
+    with the CPU oracle's own rate on a bounded sample of the same points as the baseline.
+    (Parity with the oracle on sampled points of these full-size runs is in
+    tests/test_gpu_fullsize.py.)"""
+    import torch
+    import synth
+    import paper_2409_07232_gb300 as pkg
+
+    def row(cfg_name, w, precision, steps, warmup, graph, note=""):
+        r = run_form(pkg, torch, w, precision, steps, warmup, graph=graph)
+        with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
+            ds = fc.upload(w.state(copy=False))
+            fc.step(ds, w.dt, w.n_steps)
+            _, out = fc.download(ds)
+        act = (out["status"] & 6) == 0
+        kms = r.get("coal_ms") or r.get("step_ms_graph")
+        pairs = pairs_per_active(w) * w.n_steps / (kms / 1e3)
+        line = dict(config=cfg_name, bins=sorted(set(int(b) for b in w.bins_per_grid)),
+                    form=("FP64 plain" if precision == 0 else "FP32 split") + (", graph" if graph else ""),
+                    points=w.n_points, active_points=int(r["n_active"]), points_per_s=r["value"],
+                    pairs_per_s=pairs, roofline_frac=pairs / alu_peak_pairs(precision, 2070.0),
+                    mass_error_max=float(out["mass_error"][act].max()) if act.any() else 0.0,
+                    cpu_baseline=None if args.no_cpu else cpu_sample_run(w, budget_s=8.0), note=note)
+        print(json.dumps(line), flush=True)
+
+    w1 = synth.config1()
+    row("1", w1, pkg.FSBM_FP64, 2, 3, False, "Golovin b = 1500, dt = 1 s x 100 steps")
+    row("3", w1, pkg.FSBM_FP32_SPLIT, 2, 3, True, "config 1 in the FP32 split form")
+    w4 = synth.config4()
+    row("4", w4, pkg.FSBM_FP32_SPLIT, 1, 3, True, "2M ragged points, 33-264 bins; pairs over whole species ranges")
+    del w4
+    w5 = synth.config5(n_points=100_000)
+    row("5", w5, pkg.FSBM_FP32_SPLIT, 1, 3, True, "100k of the 500k points (independent points)")
+    row("5", synth.subset(w5, np.arange(5_000)), pkg.FSBM_FP64, 1, 3, False, "5k of the 500k points")
+
+
 def pairs_per_active(w):
     """Bin pairs per collision step summed over the active points (every bin active)."""
     act = (w.species_mask > 0)
@@ -423,6 +461,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32 and 264-bin side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--table", action="store_true",
+                    help="one line per configuration (1-5) with rates, roofline fraction and parity against "
+                         "the oracle on a sample (not the default bench line)")
     ap.add_argument("--replicas", type=int, default=1,
                     help="with R > 1: R contexts share the GPU, each on a slab of the domain; prints their "
                          "aggregate rate beside one batched context (not the default bench line)")
@@ -442,6 +483,8 @@ def main():
         return reference_arm(args, world, rank)
     if args.replicas > 1:
         return main_replicas(args)
+    if args.table:
+        return main_table(args)
 
     import torch
     import paper_2409_07232_gb300 as pkg

@@ -27,7 +27,7 @@ def test_golovin_33bin_100_steps(cfg1, precision):
     got, out, _ = run_gpu(w, precision)
     err = assert_parity(w, got, out, ref, ref_out, precision)
     assert out["mass_error"].max() <= (1e-13 if precision == pkg.FSBM_FP64 else 1e-6)
-    print(f"precision {precision}: max rel L1 {err.max():.3e}")
+    print(f"golovin precision {precision}: max rel L1 {err.max():.3e}, max mass error {out['mass_error'].max():.2e}")
 
 
 @pytest.fixture(scope="module")
@@ -40,8 +40,9 @@ def conus_sample():
 def test_conus_33bin_5species_sample(conus_sample, precision):
     w, (ref, ref_out) = conus_sample
     got, out, stats = run_gpu(w, precision)
-    assert_parity(w, got, out, ref, ref_out, precision)
+    err = assert_parity(w, got, out, ref, ref_out, precision)
     assert stats["n_active"] == int(((ref_out["status"] & 6) == 0).sum())
+    print(f"conus sample precision {precision}: max rel L1 {err.max():.3e}, max mass error {out['mass_error'].max():.2e}")
 
 
 @pytest.fixture(scope="module")
@@ -54,7 +55,8 @@ def ragged_sample():
 def test_ragged_33_to_264_bins(ragged_sample, precision):
     w, (ref, ref_out) = ragged_sample
     got, out, _ = run_gpu(w, precision)
-    assert_parity(w, got, out, ref, ref_out, precision)
+    err = assert_parity(w, got, out, ref, ref_out, precision)
+    print(f"ragged precision {precision}: max rel L1 {err.max():.3e}, max mass error {out['mass_error'].max():.2e}")
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +69,8 @@ def stress_sample():
 def test_264bin_5species_20_steps(stress_sample, precision):
     w, (ref, ref_out) = stress_sample
     got, out, _ = run_gpu(w, precision)
-    assert_parity(w, got, out, ref, ref_out, precision)
+    err = assert_parity(w, got, out, ref, ref_out, precision)
+    print(f"264-bin precision {precision}: max rel L1 {err.max():.3e}, max mass error {out['mass_error'].max():.2e}")
 
 
 @pytest.mark.parametrize("precision", FORMS)
