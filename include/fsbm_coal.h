@@ -225,11 +225,12 @@ typedef struct {
  * context's precision and grows on demand (about 8.4 GB for a 425 x 300 x 50 tile with 5
  * species, 33 bins in FP64). Errors: FSBM_E_ARG for ranges outside the memory ranges, an
  * unknown grid or no species; FSBM_E_OOM if the buffer cannot be allocated. */
-FSBM_API fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* ctx, const fsbm_wrf_state* state, double dt, int32_t n_steps);
+FSBM_API fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* ctx, const fsbm_wrf_state* state, double dt,
+                                        int32_t n_steps);
 
-/* Time the collision kernel for each candidate CTA size (128, 256, 512 threads) on a copy of
- * the first 2^18 points of the given device state (all of it if smaller), three collision
- * steps of 5 s each, and keep the fastest for later steps. The caller's spectra are not
+/* Time the collision kernel for each candidate CTA size (32, 64, 128, 256, 512 threads) on a
+ * copy of the first 2^18 points of the given device state (all of it if smaller), three
+ * collision steps of 5 s each, and keep the fastest for later steps. The caller's spectra are not
  * modified. Synchronous; allocates a temporary copy of the sample. The paper has no
  * counterpart. */
 FSBM_API fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points);
@@ -240,7 +241,7 @@ FSBM_API fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* ctx, const fsbm_coal_stat
 FSBM_API fsbm_status fsbm_coal_set_graph(fsbm_coal_ctx* ctx, int32_t enable);
 
 /* Force the collision kernel's CTA size (0 = library default); for benchmarks and the
- * autotuner's tests. Valid sizes: 128, 256, 512. */
+ * autotuner's tests. Valid sizes: 32, 64, 128, 256, 512. */
 FSBM_API fsbm_status fsbm_coal_set_block(fsbm_coal_ctx* ctx, int32_t block_dim);
 
 /* Enable (1) or disable (0, the default) CUDA-event timing of the collision kernel and of

@@ -686,7 +686,9 @@ fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cands[3] = {128, 256, 512};
+  // small CTAs suit points with few species (one or two warp tasks per step): more of them
+  // fit on an SM
+  const int cands[5] = {32, 64, 128, 256, 512};
   float best = 1e30f;
   int best_b = c->block_dim;
   for (int b : cands) {
@@ -732,8 +734,8 @@ fsbm_status fsbm_coal_set_graph(fsbm_coal_ctx* c, int32_t enable) {
 fsbm_status fsbm_coal_set_block(fsbm_coal_ctx* c, int32_t block_dim) {
   if (!c) return FSBM_E_ARG;
   if (block_dim == 0) block_dim = 256;
-  if (block_dim != 128 && block_dim != 256 && block_dim != 512)
-    return fail(c, FSBM_E_ARG, "fsbm_coal_set_block: block_dim must be 128, 256 or 512");
+  if (block_dim != 32 && block_dim != 64 && block_dim != 128 && block_dim != 256 && block_dim != 512)
+    return fail(c, FSBM_E_ARG, "fsbm_coal_set_block: block_dim must be 32, 64, 128, 256 or 512");
   c->block_dim = block_dim;
   c->plan_valid = false;
   return ensure_plan(c);

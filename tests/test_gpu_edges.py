@@ -195,7 +195,7 @@ def test_autotune_leaves_state_and_agrees(precision):
         before = ds.t["spectra"].clone()
         fc.autotune(ds)
         assert bool((ds.t["spectra"] == before).all())
-        assert fc.stats()["block_dim"] in (128, 256, 512)
+        assert fc.stats()["block_dim"] in (32, 64, 128, 256, 512)
         fc.step(ds, w.dt, w.n_steps)
         got, out = fc.download(ds)
     assert_parity(w, got.astype(np.float64), out, ref, ref_out, precision)

@@ -74,7 +74,7 @@ def test_264bin_5species_20_steps(stress_sample, precision):
 
 
 @pytest.mark.parametrize("precision", FORMS)
-@pytest.mark.parametrize("block", [128, 256, 512])
+@pytest.mark.parametrize("block", [32, 64, 128, 256, 512])
 def test_block_sizes_agree(ragged_sample, precision, block):
     w, (ref, ref_out) = ragged_sample
     got, out, stats = run_gpu(w, precision, block=block)
