@@ -228,11 +228,15 @@ struct Smem {
   T* lam;         // [S][nmax]
   T* xs;          // [nmax]
   T* cd;          // [nmax] Courant number per bin distance
-  int* lim;       // [S*nmax] rows whose limiter ratio is below 1, ascending
+  T* llam;        // [S*nmax] the limited rows' ratios, ascending
+  T* lN;          // [S*nmax] their number concentrations, in the same order
+  int* lim;       // [S*nmax] rows whose limiter ratio is below 1, ascending row index
+  int* loff;      // [S*nmax] Kr offset (species id of the row's slot, bin) of the sorted rows
+  int* rk;        // [S*nmax] position of a limited row in the ratio order
   static __host__ __device__ size_t bytes(int nmax, int S) {
     size_t b = sizeof(double) * 2 * S * nmax + sizeof(Sum) * 2 * S * S * nmax;
     if (sizeof(T) != sizeof(double)) b += sizeof(T) * S * nmax;
-    b += sizeof(T) * (2 * S * nmax + 2 * nmax) + sizeof(int) * S * nmax;
+    b += sizeof(T) * (4 * S * nmax + 2 * nmax) + sizeof(int) * 3 * S * nmax;
     return (b + 15) & ~size_t(15);
   }
   __device__ void carve(unsigned char* base, int nmax, int S) {
@@ -259,7 +263,15 @@ struct Smem {
     p += sizeof(T) * nmax;
     cd = reinterpret_cast<T*>(p);
     p += sizeof(T) * nmax;
+    llam = reinterpret_cast<T*>(p);
+    p += sizeof(T) * S * nmax;
+    lN = reinterpret_cast<T*>(p);
+    p += sizeof(T) * S * nmax;
     lim = reinterpret_cast<int*>(p);
+    p += sizeof(int) * S * nmax;
+    loff = reinterpret_cast<int*>(p);
+    p += sizeof(int) * S * nmax;
+    rk = reinterpret_cast<int*>(p);
   }
 };
 
@@ -632,8 +644,9 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
 
       // 3. limited losses: loss_i = dt M_i sum_j K N_j min(lam_i, lam_j)
       //      = lam_i R_i - dt M_i sum_{j: lam_j < lam_i} (lam_i - lam_j) K N_j,
-      //    where lam_i R_i = M_i when lam_i < 1, and the correction runs only over the rows
-      //    whose ratio fired, listed in ascending order (a fixed summation order).
+      //    where lam_i R_i = M_i when lam_i < 1. The correction runs only over the rows whose
+      //    ratio fired, sorted by ratio (ties by row, a fixed order): a row then walks the
+      //    prefix of rows with smaller ratios, with no test per entry.
       if (limited) {
         if (warp == 0) {
           int cnt = 0;
@@ -648,23 +661,35 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
         }
         __syncthreads();
         const int L = s_nlim;
+        for (int q = tid; q < L; q += NT) {  // rank by counting; every entry reads the same list
+          const int r = sm.lim[q];
+          const T l = sm.lam[r];
+          int rank = 0;
+          for (int q2 = 0; q2 < L; ++q2) {
+            const T l2 = sm.lam[sm.lim[q2]];
+            rank += (l2 < l) || (l2 == l && q2 < q);
+          }
+          const int b = r / n, j = r - b * n;
+          sm.llam[rank] = l;
+          sm.lN[rank] = sm.N[r];
+          sm.loff[rank] = (s_sp[b] * n + j) * n;
+          sm.rk[r] = rank;
+        }
+        __syncthreads();
         for (int r = tid; r < E; r += NT) {
           const int a = r / n, i = r - a * n;
           if (i < s_lo[a] || i > s_hi[a]) continue;
           const T li = sm.lam[r];
+          const int cnt = li < T(1) ? sm.rk[r] : L;  // rows sorted before r have ratios <= lam_i
+          const T* __restrict__ Kri = Kr + (size_t)s_sp[a] * S * n * n + i;
+          const T* __restrict__ Krid = lev ? Sel<T>::Kr_d(G) + (size_t)s_sp[a] * S * n * n + i : nullptr;
           Acc<T> acc;
-          for (int q0 = 0; q0 < L; q0 += kLossRun) {
-            const int q1 = min(L, q0 + kLossRun);
+          for (int q0 = 0; q0 < cnt; q0 += kLossRun) {
+            const int q1 = min(cnt, q0 + kLossRun);
             for (int q = q0; q < q1; ++q) {
-              const int rj = sm.lim[q];
-              const T lj = sm.lam[rj];
-              if (lj < li) {
-                const int b = rj / n, j = rj - b * n;
-                const size_t kidx = (size_t)(s_sp[a] * S + s_sp[b]) * n * n + (size_t)j * n + i;
-                T Kv = __ldg(Kr + kidx);
-                if (lev) Kv = fma(wT, __ldg(Sel<T>::Kr_d(G) + kidx), Kv);
-                acc.add((li - lj) * Kv * sm.N[rj]);
-              }
+              T Kv = __ldg(Kri + sm.loff[q]);
+              if (lev) Kv = fma(wT, __ldg(Krid + sm.loff[q]), Kv);
+              acc.add((li - sm.llam[q]) * Kv * sm.lN[q]);  // equal ratios add exactly 0
             }
             acc.flush();
           }
