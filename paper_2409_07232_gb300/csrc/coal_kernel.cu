@@ -302,6 +302,9 @@ __device__ __forceinline__ double min_nonneg(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b) ? a : b;
 }
 __device__ __forceinline__ float min_nonneg(float a, float b) { return fminf(a, b); }
+// bit pattern of a non-negative value, ordered like the value
+__device__ __forceinline__ long long ord_bits(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ int ord_bits(float v) { return __float_as_int(v); }
 // Bott's flux with target-bin constants hoisted out of the pair loop:
 //  * bin k+1 holds at least 1e-30 of the largest content bin k can reach (Mk + 2B): then
 //    ln(rho + 1e-60) = ln M_{k+1} - ln g to 1e-30 and e^{x1/2} = sqrt(M_{k+1}) / sqrt(g);
@@ -664,10 +667,12 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
         for (int q = tid; q < L; q += NT) {  // rank by counting; every entry reads the same list
           const int r = sm.lim[q];
           const T l = sm.lam[r];
+          // ratios are positive: their bit patterns order like integers (no FP64 compares)
+          const auto lb = ord_bits(l);
           int rank = 0;
           for (int q2 = 0; q2 < L; ++q2) {
-            const T l2 = sm.lam[sm.lim[q2]];
-            rank += (l2 < l) || (l2 == l && q2 < q);
+            const auto l2b = ord_bits(sm.lam[sm.lim[q2]]);
+            rank += (l2b < lb) || (l2b == lb && q2 < q);
           }
           const int b = r / n, j = r - b * n;
           sm.llam[rank] = l;
