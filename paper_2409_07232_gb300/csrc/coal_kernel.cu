@@ -12,14 +12,15 @@
 //   2. N = M / x;  R^a_i = dt x_i N^a_i sum_{b,j} K N^b_j      (row mat-vec, lane per row);
 //      lambda = min(1, M / R) in FP64;
 //   3. loss^a_i = dt x_i N^a_i sum_{b,j} K N^b_j min(lambda^a_i, lambda^b_j)
-//      (equal to R when no ratio fired anywhere in the point: the pass is skipped);
-//   4. gain pass: for every ordered orientation (small-index species s, large-index
-//      species l) one lane per target bin k walks the bin distances d of the pairs
-//      (m - d, m) whose mass lands in k (m = k - kappa[d]), computes dM and Bott's flux F,
-//      and keeps (sum of dM - F) for bin k and (sum of F) for bin k + 1 in registers;
-//      all lanes of a warp walk the same d, so the kernel and spectrum loads are
-//      contiguous across the warp. Partial sums land in per-orientation shared arrays and
-//      are added in a fixed order: the result does not depend on scheduling;
+//      (equal to R when no ratio fired anywhere in the point: the pass is skipped; else
+//      a correction over the limited rows sorted by ratio);
+//   4. gain pass: one lane per (target bin k, ordered species orientation) item walks the
+//      bin distances d of the pairs (m - d, m) whose mass lands in k (m = k - kappa[d]),
+//      computes dM and Bott's flux F, and keeps (sum of dM - F) for bin k and (sum of F)
+//      for bin k + 1 in registers; the lanes of a warp hold one or two targets, walk the
+//      same d and read contiguous kernel entries. Partial sums land in per-orientation
+//      shared arrays and are added in a fixed order: the result does not depend on
+//      scheduling;
 //   5. M' = M - loss + gain (FP64), mass error, round-off negatives to 0, rescale to B.
 // FP32_SPLIT runs 2-4 with float values and float sums; 1 and 5 stay FP64.
 #include <algorithm>

@@ -50,14 +50,19 @@ def test_recorded_traffic_only_for_the_captured_sources(tmp_path, monkeypatch):
     t = bench.kernel_traffic(0, 1000)
     if t is not None:                                       # sources unchanged since the capture
         assert abs(t - 1000 * bench.DRAM_TRAFFIC["bytes_per_active_point"]) < 1e-6
-    copies = []
-    for i, f in enumerate(bench.KERNEL_SOURCES):
-        src = open(os.path.join(ROOT, f), "rb").read()
-        dst = tmp_path / f"k{i}"
-        dst.write_bytes(src + (b"\n// edited\n" if i == 0 else b""))
-        copies.append(str(dst))
-    monkeypatch.setattr(bench, "KERNEL_SOURCES", tuple(copies))
-    assert bench.kernel_traffic(0, 1000) is None            # any edit voids the record
+    def copies(edit):
+        out = []
+        for i, f in enumerate(bench.KERNEL_SOURCES):
+            src = open(os.path.join(ROOT, f), "rb").read()
+            dst = tmp_path / f"{edit}{i}"
+            dst.write_bytes(src + (b"\n" + edit.encode() + b"\n" if i == 0 else b""))
+            out.append(str(dst))
+        return tuple(out)
+    base = bench.kernel_code_sha256()
+    assert bench.kernel_code_sha256(copies("// a comment")) == base      # comments do not count
+    assert bench.kernel_code_sha256(copies("int edited;")) != base       # code does
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", copies("int edited;"))
+    assert bench.kernel_traffic(0, 1000) is None            # a code edit voids the record
 
 
 def test_l2_note():
