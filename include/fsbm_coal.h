@@ -63,7 +63,7 @@ typedef enum {
   FSBM_E_CUDA = -2,        /* a CUDA call failed; see fsbm_coal_last_error         */
   FSBM_E_OOM = -3,         /* device allocation failed                            */
   FSBM_E_TIMEOUT = -4,     /* reserved: a bounded device wait gave up             */
-  FSBM_E_UNSUPPORTED = -5  /* valid request this build does not implement         */
+  FSBM_E_UNSUPPORTED = -5  /* valid request the library does not implement         */
 } fsbm_status;
 
 typedef enum {
