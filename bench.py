@@ -17,10 +17,14 @@ Besides the headline number the line carries:
   roofline     the collision kernel against the ALU roofline (pairs/s against the pipe
                rate divided by the algorithmic pipe operations per pair);
   cpu_baseline the CPU oracle on a bounded sample of the same points, all host cores;
-  forms        the FP32 split form on the same domain (CUDA-graph replay) and the
-               264-bin, 5-species stress points in both forms.
+  forms        the FP32 split form on the same domain (CUDA-graph replay), the same domain
+               through the WRF-layout entry point, the 264-bin 5-species stress points in
+               both forms, the ragged 33-264-bin batch, Bott's in-place (SWEEP) order, and
+               kernels at two pressure levels.
 
 --impl reference times the CPU oracle as the reference arm (bounded sample per step).
+--table prints one line per configuration (1-5); --replicas R runs R contexts (streams or host
+processes) on slabs of the domain beside one batched context.
 Multi-GPU (torchrun): every rank runs its own seeded domain (weak scaling); the points are
 independent, so there is no collective in the data path.
 """
