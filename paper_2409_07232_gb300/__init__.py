@@ -33,6 +33,8 @@ from .binding import (  # noqa: F401
     fsbm_coal_set_timing,
     fsbm_coal_step,
     fsbm_coal_step_host,
+    fsbm_coal_step_noalloc,
+    fsbm_coal_step_wrf,
 )
 
 
