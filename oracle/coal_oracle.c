@@ -17,7 +17,8 @@
  *
  * parity pins: mass conservation, positivity, number monotonicity, K = 0 identity, one-bin
  * constant kernel, single-pair cases, power-of-two scaling, Golovin and constant-kernel
- * closed forms (tests/test_oracle_*.py).
+ * closed forms, the active range with tau > 0 and one SWEEP step written out pair by pair
+ * (tests/oracle_pins.py, tests/test_oracle_*.py).
  */
 #include "coal_oracle.h"
 

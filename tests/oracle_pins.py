@@ -20,7 +20,13 @@ What pins what:
 * scaling      -- M -> 2^e M with dt -> 2^-e dt scales the result by 2^e exactly;
 * Golovin and constant kernels -- bin masses against the closed-form solutions for an
                   exponential start, with the error shrinking as the grid is refined;
-* status       -- inactive and malformed points are left untouched and flagged.
+* status       -- inactive and malformed points are left untouched and flagged;
+* active range -- tau > 0: which bins take part (a bin exactly at the threshold, a
+                  sub-threshold bin inside the range, a bin outside it that only gains),
+                  one step written out pair by pair;
+* SWEEP by hand -- one step of Bott's in-place order on two species and three bins written
+                  out pair by pair: visiting order, the per-pair caps, the diagonal's 2 C
+                  cap and the uncapped partner bin that receives the product.
 """
 from __future__ import annotations
 
@@ -386,4 +392,112 @@ def pin_status(orc):
 FAST_PINS = [pin_identity_k0, pin_one_bin_constant, pin_single_pair, pin_mass_conservation,
              pin_positivity, pin_number_nonincreasing, pin_scaling, pin_status, pin_pressure_levels]
 SLOW_PINS = [pin_grid_tables, pin_golovin, pin_constant, pin_sweep, pin_sweep_caps_empty_exactly]
+ALL_PINS = FAST_PINS + SLOW_PINS
+
+
+def pin_active_range(orc):
+    """The active bin range with a threshold tau > 0 (the reading: the first and last bin whose
+    content is positive and at least tau times the species' largest bin; every bin between them
+    takes part, however small; bins outside collect nothing and lose nothing, but can gain).
+
+    One species on the mass-doubling grid, six bins, tau = 2^-10, largest bin 2^-20, so the
+    threshold is exactly 2^-30:
+      bin 0  empty                         -> outside
+      bin 1  2^-30, exactly at threshold   -> first active bin (M >= tau max, not >)
+      bin 2  2^-35, below threshold        -> inside the range: takes part
+      bin 3  2^-20                         -> the largest bin
+      bin 4  2^-21                         -> last active bin
+      bin 5  2^-33, below threshold        -> outside: gains, never collects
+    The kernel is zero except for three pairs. Pair (1, 3) happens only if bin 1 is in the range
+    (with the threshold taken against the species' largest bin, not its total of 1.5 * 2^-20,
+    and compared with >=). Pair (2, 4) happens only if a sub-threshold bin inside the range takes
+    part; its product lands in bin 4 and Bott's flux carries part of it into bin 5, the outside
+    bin. Pair (4, 5) must not happen: bin 5 is outside. Expected bins follow from the pair
+    bookkeeping of the pairwise step (both partners lose C x, the sum lands in bin k with
+    c = (x_i + x_j - x_k) / (x_{k+1} - x_k) = 1/4 for both pairs here) with each flux taken by
+    quadrature of the exponential profile, as in the single-pair pin."""
+    n, x0, alpha = 6, sphere_mass(2e-4), 2.0
+    x = bin_masses(n, x0, alpha)
+    tau, dt = 2.0 ** -10, 1.0
+    M = np.array([0.0, 2.0 ** -30, 2.0 ** -35, 2.0 ** -20, 2.0 ** -21, 2.0 ** -33])
+    ka, kb, ke = 2.0 ** -14, 2.0 ** -12, 2.0 ** -12
+    K = np.zeros((n, n))
+    K[1, 3], K[2, 4], K[4, 5] = ka, kb, ke      # same-species table: upper triangle read
+    w = synth.custom_points("range", 1, [(n, x0, alpha)], K, [M], [0], [1], dt, 1, tau=tau)
+    sp, out = orc.run(w)
+    N = M / x
+    # pair (1, 3): lands in bin 3 (x_1 + x_3 = 10 x_0), c = 1/4; bin 4 holds the flux's partner
+    Ca = ka * N[1] * N[3] * dt
+    dMa = Ca * (x[1] + x[3])
+    Fa = _flux_by_quadrature(dMa, M[4] / (M[3] + dMa), 0.25)
+    # pair (2, 4): lands in bin 4 (x_2 + x_4 = 20 x_0), c = 1/4; the flux goes to bin 5
+    Cb = kb * N[2] * N[4] * dt
+    dMb = Cb * (x[2] + x[4])
+    Fb = _flux_by_quadrature(dMb, M[5] / (M[4] + dMb), 0.25)
+    exp = np.array([0.0,
+                    M[1] - Ca * x[1],
+                    M[2] - Cb * x[2],
+                    M[3] - Ca * x[3] + dMa - Fa,
+                    M[4] - Cb * x[4] + Fa + dMb - Fb,
+                    M[5] + Fb])
+    # the changes are large against the tolerance: 22 % of bins 1 and 2, 0.36 % of bin 5
+    assert Cb * x[2] > 0.2 * M[2] and Ca * x[1] > 0.2 * M[1] and Fb > 1e-3 * M[5]
+    assert np.allclose(sp, exp, rtol=1e-12, atol=0.0), (sp, exp)
+    assert out["status"][0] == 0                   # no ratio fired: every loss is below its bin
+
+
+def pin_sweep_hand_case(orc):
+    """One SWEEP step (Bott's in-place order) on two species and three mass-doubling bins, written
+    out pair by pair. The kernel is zero except for four pairs; in visiting order (species pairs
+    (0,0), (0,1), (1,1); then i ascending; then j ascending):
+      X  drop bin 0 + ice bin 2: the sum (5 x_0) passes the top, lands in ice bin 2, the partner's
+         own bin (product species b, k = j): no cap on that bin, so C is not cut to M_ice2 / x_2
+         even though C x_2 is 30 times M_ice2; the partner bin ends at M + C x_0;
+      B  drop bin 1 + ice bin 1: the sum (4 x_0) is exactly ice bin 2; the drop bin's cap
+         C x_1 <= M_drop1 decides and empties it exactly; the ice bin loses C x_1;
+      C  drop bin 1 + ice bin 2: visited after B (j ascending) and finds drop bin 1 empty: nothing;
+      E  ice bin 0 with itself: the diagonal cap 2 C x_0 <= M_ice0 decides (a bin pairing with
+         itself loses two particles per collision), the bin empties exactly and its mass lands one
+         bin up with c = 0 (no flux).
+    Every transfer keeps the total, so the closing renormalisation is 1 to rounding."""
+    n, x0, alpha = 3, sphere_mass(2e-4), 2.0
+    x = bin_masses(n, x0, alpha)
+    dt = 1.0
+    m00, m01, m02 = 1e-6, 1e-8, 3e-7       # drops
+    m10, m11, m12 = 2e-8, 5e-7, 1e-9       # ice
+    kx, kb, kc, ke = 1e-3, 1e-3, 1e-3, 1e-2
+    K00, K01, K11 = np.zeros((n, n)), np.zeros((n, n)), np.zeros((n, n))
+    K01[0, 2], K01[1, 1], K01[1, 2] = kx, kb, kc     # K01[i][j]: drop bin i with ice bin j
+    K11[0, 0] = ke
+    kern = np.concatenate([K00.ravel(), K01.ravel(), K11.ravel()])
+    M = np.array([[m00, m01, m02], [m10, m11, m12]])
+    w = synth.custom_points("sweep-hand", 2, [(n, x0, alpha)], kern, [M], [0], [3], dt, 1)
+    sp, out = orc.run(w, mode=1)
+    d, ice = [m00, m01, m02], [m10, m11, m12]
+    # X: uncapped (C x_0 is 0.75 % of the drop bin; the partner bin is exempt)
+    C = kx * (d[0] / x[0]) * (ice[2] / x[2]) * dt
+    assert C * x[2] > 20 * ice[2] and C * x[0] < 0.01 * d[0]
+    d[0] -= C * x[0]
+    ice[2] += C * x[0]
+    # B: the drop bin's cap decides (C would be 7.5 times it; the ice cap is 6.7 times larger)
+    Creq = kb * (d[1] / x[1]) * (ice[1] / x[1]) * dt
+    assert Creq > 5 * d[1] / x[1] and d[1] / x[1] < ice[1] / x[1]
+    C = d[1] / x[1]
+    ice[1] -= C * x[1]
+    ice[2] += C * (x[1] + x[1])
+    d[1] = 0.0
+    # C: drop bin 1 is empty now
+    # E: the diagonal cap decides (C would be 3 times it)
+    Creq = 0.5 * ke * (ice[0] / x[0]) ** 2 * dt
+    assert 2 * Creq * x[0] > 2 * ice[0]
+    C = ice[0] / (2.0 * x[0])
+    ice[1] += C * (x[0] + x[0])
+    ice[0] = 0.0
+    exp = np.array(d + ice)
+    assert np.allclose(sp, exp, rtol=1e-13, atol=0.0), (sp, exp)
+    assert sp[1] == 0.0 and sp[3] == 0.0            # capped bins end at exactly 0
+    assert out["status"][0] & 1                     # the caps count as the limiter firing
+
+
+FAST_PINS += [pin_active_range, pin_sweep_hand_case]
 ALL_PINS = FAST_PINS + SLOW_PINS
