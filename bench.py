@@ -25,8 +25,11 @@ Besides the headline number the line carries:
 --impl reference times the CPU oracle as the reference arm (bounded sample per step).
 --table prints one line per configuration (1-5); --replicas R runs R contexts (streams or host
 processes) on slabs of the domain beside one batched context.
-Multi-GPU (torchrun): every rank runs its own seeded domain (weak scaling); the points are
-independent, so there is no collective in the data path.
+Multi-GPU (torchrun): every rank builds the same batch and steps one shard of it
+(fsbm_coal_step_shard): the batch's cost-ordered active list cut into equal-cost contiguous parts,
+one per rank. Grid points are independent, so there is no collective in the data path; the only
+collectives are the max of the timings and the sum of the copied bytes. The total work is fixed
+as N grows ("scaling": "strong"); value is the whole batch's updates over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -207,24 +210,41 @@ def cpu_sample_run(w, budget_s=12.0, seed=3):
                        f"({elapsed:.1f} s, FP64 C oracle, OpenMP over points)")
 
 
-def build_workload(name, rank, points=None):
+def build_workload(name, points=None):
+    """The bench batch. Under torchrun every rank builds the same one (same seed) and steps its
+    own equal-cost shard of it."""
     import synth
 
-    off = rank_seed_offset(rank)
     if name == "conus":
         if points:
-            return synth.conus_sample(points, points // 4, seed=7 + off)
-        return synth.config2(seed=2001 + off)
+            return synth.conus_sample(points, points // 4, seed=7)
+        return synth.config2(seed=2001)
     if name == "stress":
-        return synth.config5(n_points=20_000, seed=5001 + off)
+        return synth.config5(n_points=20_000, seed=5001)
     if name == "ragged":
-        return synth.config4(n_points=200_000, seed=4001 + off)
+        return synth.config4(n_points=200_000, seed=4001)
     raise ValueError(name)
 
 
-def rank_seed_offset(rank):
-    """Seed offset of a rank's own domain: ranks run independent domains (weak scaling)."""
-    return 1000 * rank
+def class_runs(order, cost):
+    """Run-length form of a cost-ordered list: (counts, costs) of its runs of equal entry cost.
+    ``order`` holds point indices in list order, ``cost`` the bin pairs per step of every point."""
+    c = np.asarray(cost, np.int64)[np.asarray(order, np.int64)]
+    if c.size == 0:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    starts = np.concatenate([[0], np.nonzero(np.diff(c))[0] + 1])
+    counts = np.diff(np.concatenate([starts, [c.size]]))
+    return counts.astype(np.int64), c[starts].astype(np.int64)
+
+
+def rank_shard(order, cost, world, rank):
+    """Point indices of rank ``rank``'s shard of a cost-ordered active list: the list cut into
+    ``world`` contiguous parts of near-equal cost by the library's own bound rule."""
+    import paper_2409_07232_gb300 as pkg
+
+    counts, costs = class_runs(order, cost)
+    b = pkg.fsbm_coal_shard_bounds(counts, costs, world)
+    return np.asarray(order)[b[rank]:b[rank + 1]], b
 
 
 def aggregate_times(values, dist=None, device="cpu"):
@@ -238,14 +258,34 @@ def aggregate_times(values, dist=None, device="cpu"):
     return [float(v) for v in t]
 
 
-def whole_job_rate(units_per_rank, world, ms_max):
-    """Units all ranks processed divided by the slowest rank's time."""
-    return units_per_rank * world / (ms_max / 1e3)
+def aggregate_sums(values, dist=None, device="cpu"):
+    """Sum over ranks of each value (byte counts of the ranks' own copies)."""
+    if dist is None:
+        return list(values)
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [int(v) for v in t]
 
 
-def time_steps(fc, ds, w, steps, warmup, stream, torch, barrier=None):
+def synth_subset(w, idx):
+    import synth
+
+    return synth.subset(w, np.sort(np.asarray(idx, np.int64)))
+
+
+def time_steps(fc, ds, w, steps, warmup, stream, torch, barrier=None, shard=None):
+    """Warm-up calls, then ``steps`` timed calls between CUDA events on the context's stream.
+    ``shard`` = (rank, world) steps that rank's shard of the batch (fsbm_coal_step_shard)."""
+    def one():
+        if shard and shard[1] > 1:
+            fc.step_shard(ds, w.dt, w.n_steps, shard[0], shard[1])
+        else:
+            fc.step(ds, w.dt, w.n_steps)
+
     for _ in range(warmup):
-        fc.step(ds, w.dt, w.n_steps)
+        one()
     torch.cuda.synchronize()
     fc.stats()  # reset the timing totals
     if barrier:
@@ -255,7 +295,7 @@ def time_steps(fc, ds, w, steps, warmup, stream, torch, barrier=None):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        fc.step(ds, w.dt, w.n_steps)
+        one()
     e1.record(stream)
     torch.cuda.synchronize()
     if barrier:
@@ -322,6 +362,53 @@ def run_wrf_form(pkg, torch, w, precision, steps, warmup):
                 points=w.n_points, layout="[species][bin][j][k][i], i fastest; tile = whole domain")
 
 
+def slab(w, a, b):
+    """Points [a, b) of a batch as a batch of their own (contiguous: no copy of the spectra)."""
+    import dataclasses
+    off = w.offset[a:b + 1] - w.offset[a]
+    sl = slice(a, b)
+    return dataclasses.replace(
+        w, name=w.name + f"[{a}:{b}]", spectra=w.spectra[w.offset[a]:w.offset[b]], offset=off,
+        grid_id=w.grid_id[sl], species_mask=w.species_mask[sl],
+        cloudy=None if w.cloudy is None else w.cloudy[sl],
+        temperature=None if w.temperature is None else w.temperature[sl],
+        pressure=None if w.pressure is None else w.pressure[sl], meta=dict(w.meta))
+
+
+def run_replicas_form(pkg, torch, w, precision, R, steps, warmup):
+    """R replica contexts of one context (shared tables, fsbm_coal_clone), each on its own
+    stream and its own slab of the batch (contiguous along the first horizontal axis, as an MPI
+    patch decomposition splits it), all issued back to back from one host thread; beside the same
+    batch in one context on one stream. Host wall clock around all calls (the streams overlap);
+    no CUDA graph in either, so the two compare like with like."""
+    edges = np.linspace(0, w.n_points, R + 1).astype(np.int64)
+    slabs = [slab(w, int(edges[r]), int(edges[r + 1])) for r in range(R)]
+    out = {}
+    with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
+        for label, ctxs, parts in (("batched", [fc], [w]), ("replicas", [fc.clone() for _ in range(R)], slabs)):
+            dss = [c.upload(p.state(copy=False)) for c, p in zip(ctxs, parts)]
+            for c in ctxs:
+                c.set_block(256)
+            for _ in range(warmup):
+                for c, d, p in zip(ctxs, dss, parts):
+                    c.step(d, p.dt, p.n_steps)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                for c, d, p in zip(ctxs, dss, parts):
+                    c.step(d, p.dt, p.n_steps)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            n_act = sum(int(c.stats()["n_active"]) for c in ctxs)
+            out[label] = n_act * w.n_steps * steps / (t1 - t0)
+            del dss
+            if label == "replicas":
+                for c in ctxs:
+                    c.close()
+    return dict(value=out["replicas"], batched_value=out["batched"], ratio_to_batched=out["replicas"] / out["batched"],
+                replicas=R, timing="host wall clock around all streams' calls")
+
+
 def _replica_child(rank, R, args_d, barrier, q):
     """One host process of the replica measurement: its own context and stream on the shared
     GPU, its own slab of the domain, the same collision calls as the batched run."""
@@ -350,7 +437,7 @@ def replica_workload(args_d, rank, R):
     """Slab ``rank`` of R of the bench domain (contiguous along the first horizontal axis, the
     way an MPI patch decomposition splits it), or the whole domain for R = 1."""
     import synth
-    w = build_workload("conus", 0, args_d["points"])
+    w = build_workload("conus", args_d["points"])
     if R == 1:
         return w
     edges = np.linspace(0, w.n_points, R + 1).astype(np.int64)
@@ -361,7 +448,7 @@ def main_replicas(args):
     """Throughput of R contexts sharing the GPU against one batched context on the same domain.
 
     mode "streams": one host process, R contexts on R CUDA streams, calls issued back to back.
-    mode "processes": R host processes (the paper's several MPI ranks per GPU, Sec. VI-A),
+    mode "processes": R host processes (the paper's several MPI ranks per GPU, Sec. VII-A),
     each with its own CUDA context; without MPS the GPU time-slices between them."""
     import multiprocessing as mp
     import torch
@@ -514,27 +601,32 @@ def main():
             dist.barrier()
 
     precision = pkg.FSBM_FP64 if args.precision == "fp64" else pkg.FSBM_FP32_SPLIT
-    w = build_workload(args.workload, rank, args.points)
-    n_pairs = pairs_per_active(w)
+    w = build_workload(args.workload, args.points)  # the same batch on every rank
+    cost = w.pairs_per_step()
 
     with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
         ds = fc.upload(w.state(copy=False))
         fc.autotune(ds)  # picks the CTA size on a copy of a sample of the batch
         fc.set_timing(True)
         with Clocks(local) as clk:
-            ms, st = time_steps(fc, ds, w, args.steps, args.warmup, fc.stream, torch, barrier)
+            ms, st = time_steps(fc, ds, w, args.steps, args.warmup, fc.stream, torch, barrier, shard=(rank, world))
         clocks = clk.summary()
-        n_active = st["n_active"]
+        n_active = st["n_active"]                      # active points of the whole batch
+        order = fc.active_list(w.n_points)             # the batch's cost-ordered active list
+        own = order[st["shard_begin"]:st["shard_end"]]  # this rank's part of it
+        n_pairs = int(cost[own].sum())
         coal_ms = st["coal_ms"] / max(st["coal_launches"], 1)
-        # end to end through the host-pointer entry point (pinned buffers)
-        host = {k: v for k, v in w.state(copy=False).items() if v is not None}
+        # end to end through the host-pointer entry point (pinned buffers): the rank's own
+        # points, gathered once from the host batch as a model rank would hold them
+        hw = w if world == 1 else synth_subset(w, own)
+        host = {k: v for k, v in hw.state(copy=False).items() if v is not None}
         np_dtype = np.float64 if precision == pkg.FSBM_FP64 else np.float32
         pinned = {}
         for k, v in host.items():
             arr = np.ascontiguousarray(v, np_dtype if k == "spectra" else v.dtype)
             t = torch.from_numpy(arr).pin_memory()
             pinned[k] = t.numpy()
-        out_bytes = w.n_points * (8 + 8 + 4)
+        out_bytes = hw.n_points * (8 + 8 + 4)
         h2d = sum(a.nbytes for a in pinned.values())
         d2h = pinned["spectra"].nbytes + out_bytes
         fc.step_host(pinned, w.dt, w.n_steps)  # first call sizes the device mirrors
@@ -546,8 +638,10 @@ def main():
         barrier()
 
     ms_max, e2e_max = aggregate_times([ms, e2e_s], dist, device="cuda")
-    value = whole_job_rate(n_active * w.n_steps * args.steps, world, ms_max)
-    units = n_active * w.n_steps * args.steps * world
+    h2d_all, d2h_all = aggregate_sums([h2d, d2h], dist, device="cuda")
+    # every active point of the batch is stepped by exactly one rank
+    units = n_active * w.n_steps * args.steps
+    value = units / (ms_max / 1e3)
 
     sm_mhz = clocks["sm_mhz"] or 2070.0
     achieved = n_pairs * w.n_steps / (coal_ms / 1e3) / 1e9
@@ -561,7 +655,7 @@ def main():
         "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong",
         "vs_baseline": None,
         "dtype": "f64" if precision == pkg.FSBM_FP64 else "f32+f64",
         "data": "synthetic (seeded CONUS-12km-shaped blob cloud mask, log-normal spectra, gravitational-like kernels)",
@@ -576,15 +670,16 @@ def main():
             "collision_steps_per_call": w.n_steps,
             "bin_pairs_per_call": n_pairs * w.n_steps,
             "l2": l2_note(w.spectra.size * (8 if precision == 0 else 4)),
-            "parallelism": f"dp{world} (independent points, weak scaling)",
+            "parallelism": f"dp{world}: one batch, its cost-ordered active list cut into {world} equal-cost "
+                           "shards, one per GPU, no exchange (independent points)",
         },
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
-        "e2e": {"value": units / e2e_max, "unit": "grid-point coal updates/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": 4 * args.steps,
+        "e2e": {"value": units / e2e_max, "unit": "grid-point coal updates/s", "h2d_bytes_per_step": h2d_all,
+                "d2h_bytes_per_step": d2h_all},
+        "gpu_launches": (4 if world == 1 else 5) * args.steps,
         "block_dim": st["block_dim"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                     "frac": achieved / peak, "traffic": kernel_traffic(precision, n_active),
+                     "frac": achieved / peak, "traffic": kernel_traffic(precision, len(own)),
                      "kernel": "k_coal<%s>" % ("double" if precision == 0 else "float"),
                      "peak_basis": "FP64 pipe %d/clk/SM / %d FP64 ops per pair" % (FP64_PER_CLK, FP64_OPS_PER_PAIR)
                      if precision == 0 else "min(FP32 %d/clk/SM / %d ops, MUFU %d/clk/SM / %d ops) per pair" % (
@@ -618,6 +713,11 @@ def main():
         rlv64 = run_form(pkg, torch, lv64, pkg.FSBM_FP64, 1, 3)
         if int(np.prod(w.meta.get("shape", (0,)))) == w.n_points:  # the whole domain, not a sample
             forms["conus_33bin_fp32_split_wrf_layout"] = run_wrf_form(pkg, torch, w, pkg.FSBM_FP32_SPLIT, 2, 3)
+        # several replicas of one context on their own streams, each on a slab of the domain (the
+        # paper's several ranks per GPU), against the batched call
+        for R in (2, 4):
+            forms[f"conus_33bin_fp32_split_replicas_streams_{R}"] = run_replicas_form(
+                pkg, torch, w, pkg.FSBM_FP32_SPLIT, R, 2, 3)
         for key, rr, ww, pr in (("stress_264bin_fp32_split_graph", r32, st32, 1),
                                 ("stress_264bin_fp64", r64, st64, 0),
                                 ("ragged_33to264bin_fp32_split_graph", rrag, rag, 1),
@@ -635,9 +735,9 @@ def main():
             forms[key] = rr
         fr = forms["conus_33bin_fp32_split_graph" if precision == 0 else "conus_33bin_fp64"]
         kms = fr.get("coal_ms") or fr.get("step_ms_graph")
-        fr["alu_frac"] = (n_pairs * w.n_steps / (kms / 1e3)) / alu_peak_pairs(1 - precision, sm_mhz)
+        fr["alu_frac"] = (pairs_per_active(w) * w.n_steps / (kms / 1e3)) / alu_peak_pairs(1 - precision, sm_mhz)
         line["forms"] = forms
-        line["gpu_launches"] = 4 * args.steps
+        line["gpu_launches"] = (4 if world == 1 else 5) * args.steps
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_sample_run(w)
     if rank == 0:
@@ -653,7 +753,7 @@ def reference_arm(args, world, rank):
     import oracle
     import synth
 
-    w = build_workload(args.workload, 0)
+    w = build_workload(args.workload)
     cores = oracle.max_threads()
     act = np.nonzero((w.cloudy > 0) & (w.species_mask > 0))[0]
     rng = np.random.default_rng(11)
@@ -685,7 +785,7 @@ def reference_arm(args, world, rank):
         "metric": "grid-point coal updates/s at 33 & 264 bins; FP32 batched vs FP64 plain, same GPU",
         "value": value, "unit": "grid-point coal updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "CONUS-12km-shaped 425x300x50 domain, 15% cloudy, 33 bins, 5 species, "
                                "dt=5 s x 10 collision steps per call", "form": "CPU oracle (FP64)",
                    "sample": sample},

@@ -6,9 +6,9 @@
  * coalescence) update that WRF's Fast Spectral Bin Microphysics performs per grid point in
  * coal_bott_new (arXiv 2409.07232, Sec. III, Listing 1). Collisions run only at points
  * warmer than t_min_K (Listing 1: TT > 223.15 K), with pair collection kernels tabulated
- * per species pair (Sec. V-A, Listing 2) and read per entry (Listing 4), over mass bins
+ * per species pair (Sec. VI-A, Listing 3) and read per entry (Listing 5), over mass bins
  * whose count the paper puts at 33, extendable to a few hundred (Sec. I); the cost is
- * quadratic in the bin count (Sec. V-A). Grid points are independent (Sec. V-A).
+ * quadratic in the bin count (Sec. VI-A). Grid points are independent (Sec. VI-A).
  *
  * The arithmetic is Bott's flux method in the pairwise form: per step, with every pair of
  * active bins reading start-of-step values,
@@ -38,7 +38,8 @@
  *    return FSBM_E_CUDA; a message is kept for fsbm_coal_last_error. Bad data inside a
  *    point (NaN, Inf, negative bins, an unknown grid id, a species mask or spectrum length
  *    that does not match) never traps: the point is left unchanged and flagged in status.
- *  - Thread safety: one context per host thread.
+ *  - Thread safety: a context (or a replica, fsbm_coal_clone) is used by one host thread at a
+ *    time; different contexts and replicas may be used from different threads concurrently.
  */
 #ifndef FSBM_COAL_H
 #define FSBM_COAL_H
@@ -82,7 +83,7 @@ typedef enum {
                            predecessors left, with per-pair caps C x_i <= M_i and
                            C x_j <= M_j (none on bin j when the product lands there; 2 C x_i
                            <= M_i on the diagonal). One thread per point, the paper's own
-                           mapping (Sec. V-B). FP64 only.                                  */
+                           mapping (Sec. VI-B). FP64 only.                                  */
 } fsbm_mode;
 
 /* Per-point status bits written by fsbm_coal_step. */
@@ -113,13 +114,13 @@ typedef struct {
   int32_t mode;                 /* fsbm_mode: FSBM_PAIRWISE or FSBM_SWEEP (FP64 only;
                                    FSBM_SWEEP with FSBM_FP32_SPLIT: FSBM_E_UNSUPPORTED;
                                    any other value: FSBM_E_ARG)                            */
-  /* Kernels at two pressure levels (Sec. V-A, Listing 2: FSBM forms each collision table
+  /* Kernels at two pressure levels (Sec. VI-A, Listing 3: FSBM forms each collision table
    * from a 750 mb and a 500 mb table). NULL: `kernels` is used as is and pressures are
    * ignored. Otherwise `kernels` holds the tables at p1_hpa and kernels_p2 (host FP64, same
    * layout, finite, >= 0) those at p2_hpa, and a point at pressure p collides with
    *   K = K1 + w (K2 - K1),  w = (p1 - p) / (p1 - p2) clamped to [0, 1]
    * (linear between the levels, constant outside; the paper elides the formula). The tables
-   * are read on demand per pair (Listing 4), one extra load and multiply-add each.         */
+   * are read on demand per pair (Listing 5), one extra load and multiply-add each.         */
   const double* kernels_p2;
   double p1_hpa;                /* finite; p1_hpa != p2_hpa when kernels_p2 is set         */
   double p2_hpa;
@@ -157,6 +158,10 @@ typedef struct {
   int64_t coal_launches;        /* collision-kernel launches timed                        */
   double step_ms;               /* whole-step time (compaction + collision, any mode)     */
   int64_t steps_timed;          /* steps timed                                            */
+  int64_t shard_begin;          /* the part [shard_begin, shard_end) of the ordered list of
+                                   active points (fsbm_coal_get_active_list) the last step
+                                   ran; [0, n_active) unless it was fsbm_coal_step_shard    */
+  int64_t shard_end;
 } fsbm_coal_stats;
 
 /* Build a context: validates the configuration, derives every grid's pair tables (target
@@ -165,10 +170,46 @@ typedef struct {
  * stream). Synchronises the stream before returning. *out receives the context. */
 FSBM_API fsbm_status fsbm_coal_init(const fsbm_coal_config* config, void* stream, fsbm_coal_ctx** out);
 
+/* A replica of a context for another stream (NULL = the default stream). The paper runs
+ * several MPI ranks per GPU, each with its own share of the domain (Sec. VII-A); replicas are
+ * that mapping inside one process: they share the context's device tables (nothing is copied or
+ * allocated by this call) and each has its own stream, scratch, launch plan, CUDA graph and
+ * timing, so replicas step their own batches concurrently on their own streams, from one host
+ * thread or several (each replica used by one thread at a time). The tables are freed when the
+ * context and all its replicas are destroyed, in any order. fsbm_coal_step_noalloc uses one
+ * library-wide array: replicas calling it must not overlap on the GPU. The context's device must
+ * be current when a replica steps. */
+FSBM_API fsbm_status fsbm_coal_clone(const fsbm_coal_ctx* ctx, void* stream, fsbm_coal_ctx** out);
+
 /* Advance n_points points by n_steps steps of length dt (>= 0, finite) on the context's
  * stream. Inputs and outputs are device pointers (see fsbm_coal_state). */
 FSBM_API fsbm_status fsbm_coal_step(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points,
                            double dt, int32_t n_steps);
+
+/* One shard of a batch split across several GPUs (one process and one context per GPU, each
+ * holding the whole batch's inputs). Grid points are independent (Sec. VI-A: no dependence
+ * between the grid points of the collision loop), so the batch splits with no exchange between
+ * the shards. Every shard classifies and orders all n_points exactly as fsbm_coal_step does (the
+ * compaction pass, costliest class first), cuts the ordered list of active points into n_shards
+ * contiguous parts of near-equal cost (bin pairs per collision step; every part lies within one
+ * point's cost of the total over n_shards, the bounds fsbm_coal_shard_bounds returns), and
+ * steps part `shard` only. Points of the other parts are left unchanged and their outputs are
+ * not written; skipped points (inactive, bad input) get their outputs in every shard. The
+ * union of the n_shards calls' results equals one fsbm_coal_step call's, bit for bit.
+ * 0 <= shard < n_shards <= 1024, else FSBM_E_ARG. fsbm_coal_get_stats reports the part's list
+ * positions (shard_begin, shard_end). */
+FSBM_API fsbm_status fsbm_coal_step_shard(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points,
+                                          double dt, int32_t n_steps, int32_t shard, int32_t n_shards);
+
+/* The shard bounds fsbm_coal_step_shard uses, on the host (no context, no GPU): a cost-ordered
+ * list of n_runs runs, run r holding run_count[r] entries of cost run_cost[r] each (both >= 0),
+ * is cut into n_shards contiguous parts; bounds[q] (q = 0..n_shards, caller-owned) is the first
+ * position whose cost prefix reaches ceil(q T / n_shards), T the total cost. Part q is
+ * [bounds[q], bounds[q+1]); its cost differs from T / n_shards by less than the largest entry
+ * cost plus one. FSBM_E_ARG for negative sizes, n_shards outside [1, 1024], or a total cost at
+ * or above 2^62 / n_shards. */
+FSBM_API fsbm_status fsbm_coal_shard_bounds(const int64_t* run_count, const int64_t* run_cost, int32_t n_runs,
+                                            int32_t n_shards, int64_t* bounds);
 
 /* Same as fsbm_coal_step with every fsbm_coal_state pointer in HOST memory: the arrays are
  * copied to context-owned device buffers, stepped, and the spectra and outputs copied back.
@@ -187,15 +228,19 @@ FSBM_API fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* ctx, const fsbm_coal_sta
  * batches return FSBM_E_ARG. The context's device must be current. The first call on a
  * device looks the array up (cudaGetSymbolAddress): make it before any stream capture. All
  * calls share the array, so calls that overlap on the GPU (different streams or threads) race
- * and must be serialised by the caller. fsbm_coal_get_stats and fsbm_coal_get_active_list
- * report fsbm_coal_step's own scratch, not this array. */
+ * and must be serialised by the caller. It is never captured in a CUDA graph by the library
+ * or timed (fsbm_coal_set_graph and fsbm_coal_set_timing do not apply to it), and
+ * fsbm_coal_get_stats and fsbm_coal_get_active_list report fsbm_coal_step's own scratch, not
+ * this array. The array's device address is looked up once per device and kept: after a
+ * cudaDeviceReset the library must be reloaded before this entry point is used again. Errors
+ * name this entry point in fsbm_coal_last_error. */
 FSBM_API fsbm_status fsbm_coal_step_noalloc(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points,
                                             double dt, int32_t n_steps);
 
 /* Bin fields in WRF's own memory layout (Sec. I: a patch's arrays span the memory ranges
  * ims:ime, kms:kme, jms:jme, and a thread works on a tile its:ite, kts:kte, jts:jte inside
  * them; Sec. III, Listing 1: the collision step runs at every tile point (i, k, j) warmer than
- * t_min_K; Sec. V-B, Listing 5: a predicate array kept from the loop fission says where the
+ * t_min_K; Sec. VI-B, Listing 6: a predicate array kept from the loop fission says where the
  * collision step is called). Ranges are inclusive, in the caller's index space (Fortran's
  * 1-based indices work as they are). All pointers are device pointers, caller-owned.        */
 typedef struct {

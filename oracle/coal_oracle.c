@@ -8,9 +8,9 @@
  * What the paper fixes: the routine is the per-grid-point collision-coalescence update
  * coal_bott_new (Sec. III, Listing 1), called only where T > 223.15 K (Listing 1), over
  * nkr = 33 mass bins extendable to a few hundred (Sec. I), whose cost is quadratic in the
- * bin count (Sec. V-A). Each species pair has its own tabulated collection kernel such as
- * cwls, cwlg (Sec. V-A, Listing 2), read one entry at a time (Listing 4). Grid points are
- * independent (Sec. V-A, Codee's dependency analysis).
+ * bin count (Sec. VI-A). Each species pair has its own tabulated collection kernel such as
+ * cwls, cwlg (Sec. VI-A, Listing 3), read one entry at a time (Listing 5). Grid points are
+ * independent (Sec. VI-A, Codee's dependency analysis).
  *
  * What the paper leaves out is read from Bott (1998), whose flux method the routine's name
  * refers to, in the pairwise form; each reading is marked [reading] below.

@@ -7,7 +7,7 @@
  * header, table or helper with the CUDA library under paper_2409_07232_gb300/.
  *
  * The paper (arXiv 2409.07232) names the routine (coal_bott_new, Sec. III and
- * Listing 1) and its cost structure (O(m n k b^2) per task, Sec. V-A) but prints no
+ * Listing 1) and its cost structure (O(m n k b^2) per task, Sec. VI-A) but prints no
  * collision equations. The arithmetic here is Bott's (1998) flux method for the
  * stochastic collection equation, in the pairwise (Jacobi) form: every bin pair reads
  * start-of-step values, losses are limited by a per-bin ratio, and the combined mass
@@ -45,7 +45,7 @@ typedef struct {
   const int8_t* product;          /* [S][S] product species of a collision            */
   double t_min_K;                 /* collisions only where T > t_min_K                */
   double active_rel_threshold;    /* tau_act                                          */
-  /* Pressure dependence of the kernels (Sec. V-A, Listing 2: every collision array is
+  /* Pressure dependence of the kernels (Sec. VI-A, Listing 3: every collision array is
    * formed from a 750 mb and a 500 mb table). kernels_p2 == NULL: `kernels` is used as is.
    * Otherwise `kernels` holds the tables at pressure p1_hpa and kernels_p2 (same layout)
    * those at p2_hpa, and a point at pressure p uses

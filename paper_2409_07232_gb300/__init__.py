@@ -22,6 +22,7 @@ from .binding import (  # noqa: F401
     FSBM_ST_LIMITED,
     FsbmError,
     fsbm_coal_autotune,
+    fsbm_coal_clone,
     fsbm_coal_destroy,
     fsbm_coal_get_active_list,
     fsbm_coal_get_stats,
@@ -31,9 +32,11 @@ from .binding import (  # noqa: F401
     fsbm_coal_set_block,
     fsbm_coal_set_graph,
     fsbm_coal_set_timing,
+    fsbm_coal_shard_bounds,
     fsbm_coal_step,
     fsbm_coal_step_host,
     fsbm_coal_step_noalloc,
+    fsbm_coal_step_shard,
     fsbm_coal_step_wrf,
 )
 
@@ -58,7 +61,7 @@ class FsbmCoal:
     """
 
     def __init__(self, cfg: dict, precision: int = FSBM_FP64, stream=None, device: int = 0,
-                 mode: int = FSBM_PAIRWISE):
+                 mode: int = FSBM_PAIRWISE, _parent=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("FsbmCoal needs a CUDA device")
@@ -67,11 +70,21 @@ class FsbmCoal:
         torch.cuda.set_device(self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.precision = precision
+        if _parent is not None:   # a replica: the parent's tables, this object's stream
+            self._cfg, self._keep = _parent._cfg, _parent._keep
+            self.ctx = fsbm_coal_clone(_parent.ctx, self.stream.cuda_stream)
+            return
         self._cfg, self._keep = binding.make_config(
             cfg["n_species"], cfg["bins_per_grid"], cfg["x0_g"], cfg["alpha"], cfg["kernels"],
             cfg.get("product"), cfg.get("t_min_K", 223.15), cfg.get("active_rel_threshold", 0.0), precision,
             mode, cfg.get("kernels_p2"), cfg.get("p1_hpa", 750.0), cfg.get("p2_hpa", 500.0))
         self.ctx = fsbm_coal_init(self._cfg, self.stream.cuda_stream)
+
+    def clone(self, stream=None) -> "FsbmCoal":
+        """A replica sharing this context's device tables, stepping on ``stream`` (a
+        torch.cuda.Stream; default: a new one)."""
+        stream = stream if stream is not None else self.torch.cuda.Stream(self.device)
+        return FsbmCoal(None, self.precision, stream=stream, device=self.device.index, _parent=self)
 
     @property
     def spectra_dtype(self):
@@ -103,6 +116,10 @@ class FsbmCoal:
 
     def step(self, ds: DeviceState, dt: float, n_steps: int) -> None:
         fsbm_coal_step(self.ctx, ds.struct, ds.n_points, dt, n_steps)
+
+    def step_shard(self, ds: DeviceState, dt: float, n_steps: int, shard: int, n_shards: int) -> None:
+        """Step part ``shard`` of ``n_shards`` equal-cost parts of the batch (one GPU's share)."""
+        fsbm_coal_step_shard(self.ctx, ds.struct, ds.n_points, dt, n_steps, shard, n_shards)
 
     def download(self, ds: DeviceState) -> tuple:
         self.torch.cuda.synchronize(self.device)

@@ -37,8 +37,8 @@ _STATUS_NAMES = {0: "FSBM_OK", -1: "FSBM_E_ARG", -2: "FSBM_E_CUDA", -3: "FSBM_E_
                  -4: "FSBM_E_TIMEOUT", -5: "FSBM_E_UNSUPPORTED"}
 
 # Every entry point include/fsbm_coal.h declares.
-EXPORTS = ("fsbm_coal_init", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_step_noalloc", "fsbm_coal_step_wrf",
-           "fsbm_coal_autotune",
+EXPORTS = ("fsbm_coal_init", "fsbm_coal_clone", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_step_noalloc", "fsbm_coal_step_wrf",
+           "fsbm_coal_step_shard", "fsbm_coal_shard_bounds", "fsbm_coal_autotune",
            "fsbm_coal_set_graph", "fsbm_coal_set_block", "fsbm_coal_set_timing", "fsbm_coal_get_stats",
            "fsbm_coal_get_active_list", "fsbm_coal_math_check", "fsbm_coal_destroy", "fsbm_coal_last_error")
 
@@ -112,6 +112,8 @@ class fsbm_coal_stats(ctypes.Structure):
         ("coal_launches", ctypes.c_int64),
         ("step_ms", ctypes.c_double),
         ("steps_timed", ctypes.c_int64),
+        ("shard_begin", ctypes.c_int64),
+        ("shard_end", ctypes.c_int64),
     ]
 
 
@@ -132,12 +134,16 @@ def load(path: str = LIB_PATH):
         P, V = ctypes.POINTER, ctypes.c_void_p
         sig = {
             "fsbm_coal_init": ([P(fsbm_coal_config), V, P(V)], ctypes.c_int),
+            "fsbm_coal_clone": ([V, V, P(V)], ctypes.c_int),
             "fsbm_coal_step": ([V, P(fsbm_coal_state), ctypes.c_int64, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_step_host": ([V, P(fsbm_coal_state), ctypes.c_int64, ctypes.c_double, ctypes.c_int32],
                                     ctypes.c_int),
             "fsbm_coal_step_noalloc": ([V, P(fsbm_coal_state), ctypes.c_int64, ctypes.c_double, ctypes.c_int32],
                                        ctypes.c_int),
             "fsbm_coal_step_wrf": ([V, P(fsbm_wrf_state), ctypes.c_double, ctypes.c_int32], ctypes.c_int),
+            "fsbm_coal_step_shard": ([V, P(fsbm_coal_state), ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+            "fsbm_coal_shard_bounds": ([V, V, ctypes.c_int32, ctypes.c_int32, V], ctypes.c_int),
             "fsbm_coal_autotune": ([V, P(fsbm_coal_state), ctypes.c_int64], ctypes.c_int),
             "fsbm_coal_set_graph": ([V, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_set_block": ([V, ctypes.c_int32], ctypes.c_int),
@@ -205,6 +211,13 @@ def fsbm_coal_init(config: fsbm_coal_config, stream: int = 0) -> ctypes.c_void_p
     return ctx
 
 
+def fsbm_coal_clone(ctx, stream: int = 0) -> ctypes.c_void_p:
+    """A replica of ``ctx`` on another stream, sharing its device tables."""
+    out = ctypes.c_void_p()
+    _check(ctx, load().fsbm_coal_clone(ctx, ctypes.c_void_p(stream or None), ctypes.byref(out)), "fsbm_coal_clone")
+    return out
+
+
 def fsbm_coal_step(ctx, state: fsbm_coal_state, n_points: int, dt: float, n_steps: int) -> None:
     _check(ctx, load().fsbm_coal_step(ctx, ctypes.byref(state), int(n_points), float(dt), int(n_steps)),
            "fsbm_coal_step")
@@ -220,6 +233,26 @@ def fsbm_coal_step_noalloc(ctx, state: fsbm_coal_state, n_points: int, dt: float
     allocation; at most 262144 points per call)."""
     _check(ctx, load().fsbm_coal_step_noalloc(ctx, ctypes.byref(state), int(n_points), float(dt), int(n_steps)),
            "fsbm_coal_step_noalloc")
+
+
+def fsbm_coal_step_shard(ctx, state: fsbm_coal_state, n_points: int, dt: float, n_steps: int, shard: int,
+                         n_shards: int) -> None:
+    """Step part ``shard`` of ``n_shards`` equal-cost parts of the batch's ordered active list."""
+    _check(ctx, load().fsbm_coal_step_shard(ctx, ctypes.byref(state), int(n_points), float(dt), int(n_steps),
+                                            int(shard), int(n_shards)), "fsbm_coal_step_shard")
+
+
+def fsbm_coal_shard_bounds(run_count, run_cost, n_shards: int) -> np.ndarray:
+    """Bounds (n_shards + 1 list positions) of the equal-cost parts of a list of runs, run r
+    holding run_count[r] entries of cost run_cost[r] each. Host only: no context, no GPU."""
+    cnt = np.ascontiguousarray(run_count, np.int64)
+    cost = np.ascontiguousarray(run_cost, np.int64)
+    if cnt.shape != cost.shape:
+        raise ValueError("run_count and run_cost differ in length")
+    out = np.zeros(int(n_shards) + 1, np.int64)
+    _check(None, load().fsbm_coal_shard_bounds(cnt.ctypes.data, cost.ctypes.data, int(cnt.size), int(n_shards),
+                                               out.ctypes.data), "fsbm_coal_shard_bounds")
+    return out
 
 
 def make_wrf_state(ff, mem, tile, grid=0, temperature=None, predicate=None, pressure=None, status=None,

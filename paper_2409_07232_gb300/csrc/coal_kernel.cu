@@ -5,7 +5,7 @@
 // atomic queue head until the list is exhausted. The point's spectra live in shared memory
 // for all n_steps steps; only the first load and the final store touch the caller's buffer.
 // The pair collection kernels are read straight from the L2-resident tables (one FP64 and
-// one FP32 copy per layout), one entry per bin pair (the on-demand lookup of Listing 4).
+// one FP32 copy per layout), one entry per bin pair (the on-demand lookup of Listing 5).
 //
 // Per step (Bott's flux method, pairwise form):
 //   1. budget B = sum M (FP64, fixed reduction tree), active bin range of every species;
@@ -79,59 +79,54 @@ __device__ __forceinline__ double bott_flux(double dM, double Mk, double Mk1, do
 // ln(1e-60); the two differ only for rho within a few orders of 1e-60. ln(rho) is capped at
 // 80, above which F >= dM for every c > 0 (and F = 0 for c = 0) in either form.
 //
-// FP32 flux, fast form, with the target bin's constants (M_k, M_{k+1}, and ln M_{k+1} when
-// M_{k+1} is below FP32's normal range) hoisted out of the pair loop.
-//  * rho = M_{k+1} / g from the SFU reciprocal (2 ulp), capped at 1e38;
-//  * rho normal: ln rho = (e + log2 m) ln 2 with m in [1/sqrt2, sqrt2), where the SFU's log2
-//    has an absolute error near 2^-22.6, so ln rho keeps an absolute error near 1e-7 at any
-//    magnitude; e^{x1/2} = sqrt(rho) through the SFU reciprocal square root;
-//  * rho below the normal range: ln rho = ln M_{k+1} - ln g, e^{x1/2} from the SFU
-//    exponential (relative error near 1e-6 there, where F is either negligible or clipped);
-//  * M_{k+1} = 0: ln rho = ln 1e-60 and e^{x1/2} = 1e-30, as the clamped FP32 reading does.
-// (1 - e^{-z}) / x1 with z = c x1 is c times the series of (1 - e^{-z}) / z for |z| <= 1
-// (twelve terms) and the direct form with the SFU exponential otherwise; both are evaluated
-// and one is selected, so the lanes of a warp do not diverge.
-struct TargetF32 {
-  float Mk, Mk1, lnMk1;
-  bool empty;
-};
-__device__ __forceinline__ float bott_flux_f32(float dM, const TargetF32& tg, float c) {
-  const float g = tg.Mk + dM;
-  const float rho = fminf(__fdividef(tg.Mk1, g), 1.0e38f);
-  float x1, A;
-  if (rho >= 1.17549435e-38f) {
-    const int ix = __float_as_int(rho);
-    const int e = (ix - 0x3f3504f3) >> 23;
-    const float m = __int_as_float(ix - (e << 23));
-    x1 = fmaf((float)e, 0.693147182f, __log2f(m) * 0.693147182f);
-    A = rho * rsqrtf(rho);
-  } else if (tg.empty) {
-    x1 = kLnBottEps;
-    A = 1.0e-30f;
-  } else {
-    x1 = fmaxf(tg.lnMk1 - __logf(g), kLnBottEps);
-    A = __expf(0.5f * x1);
-  }
-  x1 = fminf(x1, 80.f);
+// One formula for every pair, with no branch, from the SFU's approximations (relative error
+// near 2^-22 each):
+//   rho = M_{k+1} / g through the SFU reciprocal; x1 = log2(rho) ln 2, clamped to
+//   [ln 1e-60, 80] (an empty bin k+1 gives rho = 0 and x1 = ln 1e-60; a ratio that overflows
+//   gives x1 = 80; a NaN from 0 / 0 takes the lower clamp);
+//   F = dM e^{x1/2} (1 - e^{-z}) / x1 with z = c x1, where
+//     (1 - e^{-z}) / x1 = c e^{-z/2} sinh(z/2) / (z/2)   for |z| <= 1 (no cancellation near
+//       z = 0: sinh(y)/y = 1 + y^2/6 + y^4/120 + y^6/5040, next term below 1.1e-8), and
+//     (1 - e^{-z}) / x1 = (1 - (e^{-z/2})^2) / x1        otherwise;
+//   both are formed and one is selected, so the lanes of a warp never diverge here.
+// Five SFU operations per pair: the two reciprocals, log2, e^{x1/2} and e^{-z/2}. They flush
+// subnormal inputs and results to zero (one SFU instruction each, no subnormal fix-up): a ratio
+// rho below FP32's normal range then reads as 0 (x1 = ln 1e-60) and a sum g below it as an
+// overflowing ratio (x1 = 80), both in bins more than 30 orders below any normal content; the
+// exponentials' results (e^{x1/2} >= 1e-30, e^{-z/2} in [e^-40, e^69]) stay normal.
+__device__ __forceinline__ float sfu_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sfu_lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sfu_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kLn2f = 0.693147182f;
+constexpr float kHalfLog2ef = 0.721347520f;  // log2(e) / 2
+__device__ __forceinline__ float bott_flux_f32(float dM, float Mk, float Mk1, float c) {
+  const float g = Mk + dM;
+  const float rho = Mk1 * sfu_rcp(g);
+  const float x1 = fminf(fmaxf(sfu_lg2(rho) * kLn2f, kLnBottEps), 80.f);
   const float z = c * x1;
-  // (1 - e^{-z}) / z = sum_k w^k / (k+1)!, w = -z, k = 0..11 (next term below 2e-10 at |z| = 1)
-  const float w = -z;
-  float q = fmaf(w, 1.f / 479001600.f, 1.f / 39916800.f);
-  q = fmaf(q, w, 1.f / 3628800.f);
-  q = fmaf(q, w, 1.f / 362880.f);
-  q = fmaf(q, w, 1.f / 40320.f);
-  q = fmaf(q, w, 1.f / 5040.f);
-  q = fmaf(q, w, 1.f / 720.f);
-  q = fmaf(q, w, 1.f / 120.f);
-  q = fmaf(q, w, 1.f / 24.f);
-  q = fmaf(q, w, 1.f / 6.f);
-  q = fmaf(q, w, 0.5f);
-  q = fmaf(q, w, 1.f);
-  // |z| > 1: 1 - e^{-z} loses at most a factor e^{-1} / (1 - e^{-1}) < 0.6 of the SFU
-  // exponential's accuracy; an overflowing e^{-z} gives ratio = +inf and F = dM (the clip)
-  const float direct = __fdividef(1.f - __expf(w), x1);
-  const float ratio = fabsf(z) <= 1.f ? c * q : direct;
-  return fminf(dM * A * ratio, dM);
+  const float A = sfu_ex2(x1 * kHalfLog2ef);    // e^{x1/2}
+  const float w = sfu_ex2(z * -kHalfLog2ef);    // e^{-z/2}
+  const float z2 = z * z;
+  float P = fmaf(z2, 1.f / 322560.f, 1.f / 1920.f);
+  P = fmaf(z2, P, 1.f / 24.f);
+  P = fmaf(z2, P, 1.f);
+  const float near0 = c * w * P;
+  const float far = fmaf(-w, w, 1.f) * sfu_rcp(x1);  // an overflowing e^{-z} gives +inf: F = dM
+  const float ratio = fabsf(z) <= 1.f ? near0 : far;
+  return fminf(dM * (A * ratio), dM);  // A * ratio first: dM * A alone can underflow; fminf
+                                       // keeps dM where dM * inf gave inf or 0 * inf NaN
 }
 
 template <typename T> struct Sel;
@@ -307,8 +302,9 @@ __device__ __forceinline__ float min_nonneg(float a, float b) { return fminf(a, 
 __device__ __forceinline__ long long ord_bits(double v) { return __double_as_longlong(v); }
 __device__ __forceinline__ int ord_bits(float v) { return __float_as_int(v); }
 // Bott's flux with target-bin constants hoisted out of the pair loop:
-//  * bin k+1 holds at least 1e-30 of the largest content bin k can reach (Mk + 2B): then
-//    ln(rho + 1e-60) = ln M_{k+1} - ln g to 1e-30 and e^{x1/2} = sqrt(M_{k+1}) / sqrt(g);
+//  * bin k+1 holds at least 1e-43 of the largest content bin k can reach (Mk + 2B): then
+//    1e-60 g is below half an ulp of M_{k+1}, M_{k+1} + 1e-60 g rounds to M_{k+1} exactly, and
+//    ln(rho + 1e-60) = ln M_{k+1} - ln g, e^{x1/2} = sqrt(M_{k+1}) / sqrt(g);
 //  * bin k+1 is empty: x1 = ln 1e-60 and e^{x1/2} = 1e-30 for every pair;
 //  * otherwise (a deep tail): x1 = ln(M_{k+1} + 1e-60 g) - ln g and e^{x1/2} =
 //    sqrt(M_{k+1} + 1e-60 g) / sqrt(g).
@@ -323,7 +319,7 @@ __device__ __forceinline__ TargetFP64 target_fp64(double Mk, double Mk1, double 
   TargetFP64 tg;
   tg.Mk = Mk;
   tg.Mk1 = Mk1;
-  tg.kind = (Mk1 >= 1e-30 * (Mk + 2.0 * B) && Mk1 >= 1e-300) ? 0 : (is_zero(Mk1) ? 1 : 2);
+  tg.kind = (Mk1 >= 1e-43 * (Mk + 2.0 * B) && Mk1 >= 1e-300) ? 0 : (is_zero(Mk1) ? 1 : 2);
   tg.lnMk1 = tg.kind == 0 ? fsbm_log(Mk1, mt) : mt.ln_eps;
   tg.sqMk1 = tg.kind == 0 ? sqrt(Mk1) : 0.0;
   return tg;
@@ -366,103 +362,83 @@ template <> struct TargetOf<double> {
   }
 };
 template <> struct TargetOf<float> {
-  TargetF32 tg;
+  float Mk, Mk1;
   __device__ __forceinline__ void init(float mk, float mk1, double, const MathTabs&) {
-    tg.Mk = mk;
-    tg.Mk1 = mk1;
-    tg.empty = is_zero(mk1);
-    tg.lnMk1 = (!tg.empty && mk1 < 1.17549435e-38f) ? logf(mk1) : 0.f;
+    Mk = mk;
+    Mk1 = mk1;
   }
   __device__ __forceinline__ float flux(float dM, float c, const MathTabs&) const {
-    return bott_flux_f32(dM, tg, c);
+    return bott_flux_f32(dM, Mk, Mk1, c);
   }
 };
 
-// Gain pass for one (target bin k, orientation o) item per lane. A lane's pairs come in
-// groups (distance class kappa, larger bin m) whose distances d form one contiguous range; the
-// lane walks all its pairs in ONE loop, one pair per iteration, stepping d and moving to the
-// next non-empty group only when a range runs out. Everything the loop reads more than once
-// (the orientation's fields, the group's constants) is copied into registers first: the
-// loop then touches shared memory only for the two spectrum values, the limiter ratio and
-// the Courant number of its pair.
+// Gain pass for one (target bin k, orientation o) item per lane. The pairs (m - d, m) whose
+// mass lands in k come in groups: for each distance class kappa (kappa(d) = kappa for d in
+// [d_lo, d_hi]) the larger bin is m = k - kappa (every m in [n-1-kappa, n-1] for the top bin,
+// which keeps what reaches or passes it, with no flux), and d runs over one contiguous range.
+// The loops are nested (class, m, d): the class loop has the same trip count in every lane, so
+// the lanes of a warp move from group to group together and only the d ranges differ (by range
+// cut-offs and by one pair between adjacent targets). Within a group the loop reads the
+// pre-scaled kernel entry (contiguous across the warp's orientations), N of the smaller bin,
+// its limiter ratio and the Courant number c(d); everything else is in registers.
+//   dM = C (x_i + x_m) = [K (1 + alpha^-d)] N_i [M_m dt]      (x_i = x_m alpha^-d)
 // LEVELS: the point lies between two pressure levels; its kernel is K1 + wl (K2 - K1).
-template <typename T, bool LIMITED, bool LEVELS>
+template <typename T, bool LIMITED, bool LEVELS, bool TOP>
 __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T>& sm, const Orient& o_ref,
-                                          const int* lo, const int* hi, int k, T dt, double B, const MathTabs& mt,
-                                          T wl, typename Num<T>::Sum* out_stay, typename Num<T>::Sum* out_up) {
+                                          const int* lo, const int* hi, int k, bool on, T dt, double B,
+                                          const MathTabs& mt, T wl, typename Num<T>::Sum* out_stay,
+                                          typename Num<T>::Sum* out_up) {
   const int n = G.n;
   const Orient o = o_ref;  // register copy
-  const int dmin = o.dmin;
-  const int kappa_max = G.kappa_max;
   Acc<T> stay, up;
   const T* __restrict__ Kd = Sel<T>::Kd(G) + o.table;
   const T* __restrict__ Kdd = LEVELS ? Sel<T>::Kd_d(G) + o.table : nullptr;
   const T* __restrict__ Ns = sm.N + o.s * n;
-  const T* __restrict__ Nl = sm.N + o.l * n;
-  const T* __restrict__ Ms = sm.Mt + o.s * n;
+  const T* __restrict__ Ml = sm.Mt + o.l * n;
   const T* __restrict__ Ls = sm.lam + o.s * n;
   const T* __restrict__ Ll = sm.lam + o.l * n;
-  const T* __restrict__ xs = sm.xs;
   const T* __restrict__ cds = sm.cd;
   const int lo_s = lo[o.s], hi_s = hi[o.s], lo_l = lo[o.l], hi_l = hi[o.l];
-  const bool valid = k >= 1 && k < n;
-  const bool top = k == n - 1;
-  // regular target: pairs with m + kappa(d) == k; top bin: every pair with m + kappa(d) >= n-1
-  // stays there without a flux
+  on = on && k >= 1 && k < n;
   TargetOf<T> tgt;
-  tgt.init(valid && !top ? sm.Mt[o.c * n + k] : T(0), valid && !top ? sm.Mt[o.c * n + k + 1] : T(0), B, mt);
+  if (!TOP) tgt.init(on ? sm.Mt[o.c * n + k] : T(0), on ? sm.Mt[o.c * n + k + 1] : T(0), B, mt);
   const int kstride = n * S2;
-  int kap = -1, m = 1, mhi = 0, d = 0, d1 = -1, ko = 0;
-  T nl = T(0), xl = T(0), ll = T(1);
-  auto next_group = [&]() -> bool {
-    for (;;) {
-      if (m > mhi) {
-        if (++kap > kappa_max) return false;
-        m = top ? max(n - 1 - kap, lo_l) : max(k - kap, lo_l);
-        mhi = top ? min(n - 1, hi_l) : min(k - kap, hi_l);
-        continue;
+  for (int kap = 0; kap <= G.kappa_max; ++kap) {
+    const int dlo = max(G.d_lo[kap], (int)o.dmin), dhi = G.d_hi[kap];
+    const int m0 = max(TOP ? n - 1 - kap : k - kap, lo_l);
+    const int m1 = on ? min(TOP ? n - 1 : k - kap, hi_l) : m0 - 1;
+    for (int m = m0; m <= m1; ++m) {
+      const int d0 = max(dlo, m - hi_s), d1 = min(dhi, m - lo_s);
+      const T am = Ml[m] * dt;
+      const T ll = LIMITED ? Ll[m] : T(1);
+      const ptrdiff_t e0 = (ptrdiff_t)(d0 * n + m) * S2;
+      const T* __restrict__ Kp = Kd + e0;
+      const T* __restrict__ Kq = LEVELS ? Kdd + e0 : nullptr;
+      // runs of up to kGainRun pairs, each folded into the running totals after it
+      for (int dc = d0; dc <= d1; dc += kGainRun) {
+        const int dce = min(d1, dc + kGainRun - 1);
+        for (int d = dc; d <= dce; ++d, Kp += kstride) {
+          const int i = m - d;
+          T K = __ldg(Kp);
+          if (LEVELS) {
+            K = fma(wl, __ldg(Kq), K);
+            Kq += kstride;
+          }
+          T dM = K * am * Ns[i];
+          if (LIMITED) dM *= min_nonneg(Ls[i], ll);
+          stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
+          if (!TOP) {    // none out of the top bin
+            const T c = cds[d];
+            // c = 0 (the pair lands exactly on bin k): F = 0. The FP32 flux gives 0 there by
+            // itself; the FP64 one is skipped (a whole group of d = 0 pairs at once)
+            if (sizeof(T) == sizeof(float) || !is_zero(c)) up.add(tgt.flux(dM, c, mt));
+          }
+        }
+        stay.flush();
+        up.flush();
       }
-      d = max(max(G.d_lo[kap], dmin), m - hi_s);
-      d1 = min(G.d_hi[kap], m - lo_s);
-      if (d <= d1) {
-        nl = Nl[m] * dt;
-        xl = xs[m];
-        if (LIMITED) ll = Ll[m];
-        ko = (d * n + m) * S2;
-        return true;
-      }
-      ++m;
-    }
-  };
-  bool live = valid && next_group();
-  int cnt = 0;
-  while (live) {
-    // one pair (m - d, m): dM = C (x_i + x_m) = K N_m dt (M_i + N_i x_m) h phi; the table
-    // entry of the same-species diagonal pair already holds h K = K / 2
-    const int i = m - d;
-    T K = __ldg(Kd + ko);
-    if (LEVELS) K = fma(wl, __ldg(Kdd + ko), K);
-    T dM = K * nl * fma(Ns[i], xl, Ms[i]);
-    if (LIMITED) dM *= min_nonneg(Ls[i], ll);
-    if (pos(dM)) {
-      const T c = cds[d];
-      stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
-      if (!top && !is_zero(c)) up.add(tgt.flux(dM, c, mt));  // none out of the top bin; c = 0: F = 0
-    }
-    ++d;
-    ko += kstride;
-    if (d > d1) {
-      ++m;
-      live = next_group();
-    }
-    if (++cnt == kGainRun) {
-      stay.flush();
-      up.flush();
-      cnt = 0;
     }
   }
-  stay.flush();
-  up.flush();
   typename Num<T>::Sum st = stay.sum(), u = up.sum();
   Num<T>::sub(st, u);
   *out_stay = st;
@@ -490,7 +466,7 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
   Smem<T> sm;
   sm.carve(smem_raw, nmax, S);
   const int tid = threadIdx.x, NT = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = NT >> 5;
-  const int n_active = counters[0];
+  const int n_end = counters[2];
   const T dtT = (T)dt;
 
   for (;;) {
@@ -498,7 +474,7 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
     __syncthreads();
     const int idx = s_next;
     __syncthreads();
-    if (idx >= n_active) break;
+    if (idx >= n_end) break;
     const int p = list[idx];
     const int g = pd.grid_id[p];
     const GridDev& G = t.g[g];
@@ -729,26 +705,32 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
             ol = q * 32 + lane;
             on = ol < O;
             ol = on ? ol : 0;
-            k = on ? n - 1 : 0;
+            k = n - 1;
           } else {
             const int f = (n_reg_tasks - 1 - (q - n_top_tasks)) * 32 + lane - pad;
             on = f >= 0;
             const int kq = on ? f / O : 0;
             ol = on ? f - kq * O : 0;
-            k = on ? kq + 1 : 0;
+            k = kq + 1;
           }
           typename Num<T>::Sum st_, up_;
+#define FSBM_GAIN(LIM, LV, TP) \
+  gain_task<T, LIM, LV, TP>(G, S * S, sm, ori[ol], s_lo, s_hi, k, on, dtT, Bs, t.math, wT, &st_, &up_)
+          const bool top_task = q < n_top_tasks;
           if (LEV && lev) {
-            if (limited)
-              gain_task<T, true, LEV>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, wT, &st_, &up_);
-            else
-              gain_task<T, false, LEV>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, wT, &st_, &up_);
+            if (limited) {
+              if (top_task) FSBM_GAIN(true, LEV, true); else FSBM_GAIN(true, LEV, false);
+            } else {
+              if (top_task) FSBM_GAIN(false, LEV, true); else FSBM_GAIN(false, LEV, false);
+            }
           } else {
-            if (limited)
-              gain_task<T, true, false>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, wT, &st_, &up_);
-            else
-              gain_task<T, false, false>(G, S * S, sm, ori[ol], s_lo, s_hi, k, dtT, Bs, t.math, wT, &st_, &up_);
+            if (limited) {
+              if (top_task) FSBM_GAIN(true, false, true); else FSBM_GAIN(true, false, false);
+            } else {
+              if (top_task) FSBM_GAIN(false, false, true); else FSBM_GAIN(false, false, false);
+            }
           }
+#undef FSBM_GAIN
           if (on) {
             sm.stay[ol * n + k] = st_;
             sm.up[ol * n + k] = up_;

@@ -2,8 +2,8 @@
 //
 // WRF calls coal_bott_new only for grid points that pass two temperature tests inside the
 // grid loop (Listing 1); the paper's loop fission records that branch outcome in a
-// predicate array and runs the collision loop over the predicate (Sec. V-B, Listing 5),
-// and notes that cloud-free points make the per-point work uneven (Sec. VII). Here the
+// predicate array and runs the collision loop over the predicate (Sec. VI-B, Listing 6),
+// and notes that cloud-free points make the per-point work uneven (Sec. VIII). Here the
 // predicate is evaluated for every point, the passing points are packed into a list, and
 // the list is ordered costliest class first (longest-processing-time order for the
 // persistent collision kernel): a stable counting sort over (grid, stored-species count)
@@ -12,8 +12,10 @@
 // Three launches, no host synchronisation, no atomics (the order is deterministic):
 //   classify  -- per point: status for skipped points, class counts per CTA;
 //   scan      -- one CTA: exclusive scan of the [class][CTA] counts, the active count,
-//                and the persistent queue's head reset to 0;
+//                and the persistent queue's head and end reset to the whole list;
 //   scatter   -- per point: its slot = class base + CTA base + rank within the CTA.
+// A sharded call (several GPUs splitting one batch) adds one single-thread launch after the
+// scan that narrows the queue to its shard of the ordered list (shard_bound).
 #include "fsbm_internal.cuh"
 
 namespace fsbm {
@@ -108,7 +110,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(int32_t* counts, int64_t 
   if (tid == kScanThreads - 1) {
     counters[0] = (int32_t)part[kScanThreads - 1];
     counters[1] = 0;
+    counters[2] = (int32_t)part[kScanThreads - 1];
+    counters[3] = 0;
   }
+}
+
+// Shard `shard` of n_shards: its bounds in the ordered list from the class sizes (the scanned
+// counts hold each class's first position in their first block's entry) and the class costs.
+// The collision kernels then take points from [counters[1], counters[2]).
+__global__ void k_shard(Tables t, const int32_t* counts, int64_t n_blocks, int32_t* counters, int shard,
+                        int n_shards) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int nb = t.G * t.S;
+  int64_t cnt[kNumBuckets], cost[kNumBuckets];
+  const int64_t n_active = counters[0];
+  for (int c = 0; c < nb; ++c) {
+    const int64_t a = counts[(int64_t)c * n_blocks];
+    const int64_t b = c + 1 < nb ? counts[(int64_t)(c + 1) * n_blocks] : n_active;
+    cnt[c] = b - a;
+    cost[c] = t.rank_cost[c];
+  }
+  const int64_t lo = shard_bound(cnt, cost, nb, n_shards, shard);
+  const int64_t hi = shard_bound(cnt, cost, nb, n_shards, shard + 1);
+  counters[1] = (int32_t)lo;
+  counters[2] = (int32_t)hi;
+  counters[3] = (int32_t)lo;
 }
 
 __global__ void __launch_bounds__(kCompactThreads) k_scatter(Tables t, PointsDev pd, int64_t n_points,
@@ -139,13 +165,14 @@ __global__ void __launch_bounds__(kCompactThreads) k_scatter(Tables t, PointsDev
 }  // namespace
 
 cudaError_t launch_compact(const Tables& t, const PointsDev& p, int64_t n_points, const Scratch& s,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, int shard, int n_shards) {
   const int64_t nblk = (n_points + kCompactThreads - 1) / kCompactThreads;
   if (nblk != s.n_blocks) return cudaErrorInvalidValue;
   if (nblk > 0) {
     k_classify<<<(unsigned)nblk, kCompactThreads, 0, stream>>>(t, p, n_points, s.block_counts, nblk);
   }
   k_scan<<<1, kScanThreads, 0, stream>>>(s.block_counts, (int64_t)t.G * t.S * nblk, s.counters);
+  if (nblk > 0 && n_shards > 1) k_shard<<<1, 32, 0, stream>>>(t, s.block_counts, nblk, s.counters, shard, n_shards);
   if (nblk > 0) {
     k_scatter<<<(unsigned)nblk, kCompactThreads, 0, stream>>>(t, p, n_points, s.block_counts, nblk,
                                                             s.active_list);

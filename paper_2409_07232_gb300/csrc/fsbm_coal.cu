@@ -2,8 +2,8 @@
 //
 // fsbm_coal_init derives every grid's pair tables and lays the tabulated pair kernels out
 // for the device once, replacing the per-call kernel filling the paper profiled in
-// kernals_ks (Sec. V-A, Listing 2) with a lookup of one entry per bin pair (Listing 4).
-// fsbm_coal_step runs the compaction pass (the predicate array of Sec. V-B, Listing 5) and
+// kernals_ks (Sec. VI-A, Listing 3) with a lookup of one entry per bin pair (Listing 5).
+// fsbm_coal_step runs the compaction pass (the predicate array of Sec. VI-B, Listing 6) and
 // the persistent collision kernel on the caller's stream, optionally as a CUDA-graph replay.
 #include <cuda_runtime.h>
 
@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -20,11 +21,20 @@
 
 using namespace fsbm;
 
+// Device tables of a context (kernel layouts, bin grids, math tables), shared by the context
+// and its replicas (fsbm_coal_clone) and freed with the last of them.
+struct TableStore {
+  std::vector<void*> allocs;
+  ~TableStore() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
 struct fsbm_coal_ctx {
   int S = 0, G = 0, precision = 0, device = 0, n_sms = 0;
   cudaStream_t stream = nullptr;
   Tables t{};
-  std::vector<void*> table_allocs;
+  std::shared_ptr<TableStore> tables = std::make_shared<TableStore>();
   // step scratch
   Scratch scratch{};
   int64_t cap_points = -1;
@@ -51,6 +61,7 @@ struct fsbm_coal_ctx {
   double g_dt = 0.0;
   int g_steps = -1;
   CoalLaunch g_plan{};
+  int g_shard = 0, g_nshards = 1;
   bool last_replayed = false;
   int64_t last_n = 0;
   // CUDA-event timing
@@ -95,7 +106,7 @@ template <typename V>
 fsbm_status upload(fsbm_coal_ctx* c, const std::vector<V>& h, const V** out) {
   void* d = nullptr;
   CU(c, cudaMalloc(&d, sizeof(V) * std::max<size_t>(h.size(), 1)));
-  c->table_allocs.push_back(d);
+  c->tables->allocs.push_back(d);
   if (!h.empty()) CU(c, cudaMemcpyAsync(d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, c->stream));
   *out = static_cast<const V*>(d);
   return FSBM_OK;
@@ -153,15 +164,16 @@ fsbm_status ensure_plan(fsbm_coal_ctx* c) {
   return FSBM_OK;
 }
 
-fsbm_status check_state(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt, int32_t n_steps) {
-  if (!s) return fail(c, FSBM_E_ARG, "fsbm_coal_step: state is NULL");
-  if (n_points < 0 || n_points > INT32_MAX - 1)
-    return fail(c, FSBM_E_ARG, "fsbm_coal_step: n_points must be in [0, 2^31 - 2]");
-  if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(c, FSBM_E_ARG, "fsbm_coal_step: dt must be finite and >= 0");
-  if (n_steps < 0) return fail(c, FSBM_E_ARG, "fsbm_coal_step: n_steps must be >= 0");
+fsbm_status check_state(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt, int32_t n_steps,
+                        const char* who = "fsbm_coal_step") {
+  const std::string w(who);
+  if (!s) return fail(c, FSBM_E_ARG, w + ": state is NULL");
+  if (n_points < 0 || n_points > INT32_MAX - 1) return fail(c, FSBM_E_ARG, w + ": n_points must be in [0, 2^31 - 2]");
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(c, FSBM_E_ARG, w + ": dt must be finite and >= 0");
+  if (n_steps < 0) return fail(c, FSBM_E_ARG, w + ": n_steps must be >= 0");
   if (n_points > 0 && (!s->spectra || !s->offset || !s->grid_id || !s->species_mask || !s->mass_budget ||
                        !s->mass_error || !s->status))
-    return fail(c, FSBM_E_ARG, "fsbm_coal_step: a required state pointer is NULL");
+    return fail(c, FSBM_E_ARG, w + ": a required state pointer is NULL");
   return FSBM_OK;
 }
 
@@ -197,9 +209,9 @@ fsbm_status take_events(fsbm_coal_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* o
 }
 
 fsbm_status enqueue(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps,
-                    const CoalLaunch& plan, bool capturing) {
+                    const CoalLaunch& plan, bool capturing, int shard, int n_shards) {
   cudaStream_t stream = capturing ? c->cap_stream : c->stream;
-  CU(c, launch_compact(c->t, p, n_points, c->scratch, stream));
+  CU(c, launch_compact(c->t, p, n_points, c->scratch, stream, shard, n_shards));
   const bool timed = c->timing && !capturing;
   std::pair<cudaEvent_t, cudaEvent_t> ev{};
   if (timed) {
@@ -215,9 +227,11 @@ fsbm_status enqueue(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, doub
   return FSBM_OK;
 }
 
-fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps);
+fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps, int shard,
+                        int n_shards);
 
-fsbm_status run_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps) {
+fsbm_status run_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps,
+                     int shard = 0, int n_shards = 1) {
   fsbm_status st = ensure_scratch(c, n_points);
   if (st != FSBM_OK) return st;
   st = ensure_plan(c);
@@ -229,7 +243,7 @@ fsbm_status run_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, dou
     if (st != FSBM_OK) return st;
     CU(c, cudaEventRecord(ev.first, c->stream));
   }
-  st = launch_step(c, p, n_points, dt, n_steps);
+  st = launch_step(c, p, n_points, dt, n_steps, shard, n_shards);
   if (st != FSBM_OK) return st;
   if (c->timing) {
     CU(c, cudaEventRecord(ev.second, c->stream));
@@ -238,13 +252,15 @@ fsbm_status run_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, dou
   return FSBM_OK;
 }
 
-fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps) {
+fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps, int shard,
+                        int n_shards) {
   if (!c->graph_enabled) {
     c->last_replayed = false;
-    return enqueue(c, p, n_points, dt, n_steps, c->plan, false);
+    return enqueue(c, p, n_points, dt, n_steps, c->plan, false, shard, n_shards);
   }
   const bool hit = c->gexec && same_points(p, c->g_points) && n_points == c->g_n && dt == c->g_dt &&
-                   n_steps == c->g_steps && std::memcmp(&c->plan, &c->g_plan, sizeof(CoalLaunch)) == 0;
+                   n_steps == c->g_steps && std::memcmp(&c->plan, &c->g_plan, sizeof(CoalLaunch)) == 0 &&
+                   shard == c->g_shard && n_shards == c->g_nshards;
   if (!hit) {
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
@@ -254,7 +270,7 @@ fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, 
     // which cannot be captured); the graph then runs on the caller's stream
     if (!c->cap_stream) CU(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     CU(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    fsbm_status est = enqueue(c, p, n_points, dt, n_steps, c->plan, true);
+    fsbm_status est = enqueue(c, p, n_points, dt, n_steps, c->plan, true, shard, n_shards);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
     if (est != FSBM_OK) {
@@ -273,6 +289,8 @@ fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, 
     c->g_dt = dt;
     c->g_steps = n_steps;
     c->g_plan = c->plan;
+    c->g_shard = shard;
+    c->g_nshards = n_shards;
   }
   CU(c, cudaGraphLaunch(c->gexec, c->stream));
   c->last_replayed = hit;
@@ -290,8 +308,7 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
   fsbm_coal_ctx* c = new fsbm_coal_ctx();
   auto bail = [&](fsbm_status s) {
     // keep the context only to report the message? no: the caller gets NULL; free everything
-    for (void* p : c->table_allocs) cudaFree(p);
-    delete c;
+    delete c;  // frees the tables allocated so far
     return s;
   };
   const int S = cfg->n_species, G = cfg->n_grids;
@@ -380,13 +397,17 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
       for (int s = 0; s < S; ++s)
         for (int l = 0; l < S; ++l) {
           double* kr = Kr.data() + (size_t)(s * S + l) * nn;
-          // Kd[d][m][s*S+l]: the orientations of one (d, m) sit side by side. The same-species
-          // diagonal pair (d = 0, s = l) is counted once with weight 1/2 (a bin collecting
-          // itself), so its entry holds K / 2 and the gain pass needs no weight.
-          for (int d = 0; d < n; ++d)
+          // Kd[d][m][s*S+l]: the orientations of one (d, m) sit side by side. Each entry is
+          // scaled by 1 + alpha^-d = (x_{m-d} + x_m) / x_m, so that the gain pass forms the
+          // pair's mass C (x_i + x_m) as entry * N_i * (M_m dt). The same-species diagonal pair
+          // (d = 0, s = l) is counted once with weight 1/2 (a bin collecting itself), so its
+          // entry holds K (1 + 1) / 2 and the gain pass needs no weight.
+          for (int d = 0; d < n; ++d) {
+            const double sd = 1.0 + std::pow(al, -(double)d);
             for (int m = d; m < n; ++m)
               Kd[((size_t)d * n + m) * S2 + (s * S + l)] =
-                  kern_entry(Kt, S, n, s, m - d, l, m) * ((d == 0 && s == l) ? 0.5 : 1.0);
+                  kern_entry(Kt, S, n, s, m - d, l, m) * sd * ((d == 0 && s == l) ? 0.5 : 1.0);
+          }
           for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) kr[(size_t)j * n + i] = kern_entry(Kt, S, n, s, i, l, j);
         }
@@ -454,6 +475,15 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
     std::memcpy(&hi, &bits, sizeof hi);
     c->t.math.ln2_hi = hi;
     c->t.math.ln2_lo = (double)(ln2 - (long double)hi);
+    std::vector<double> ebt(2 * 2048);
+    for (int b = 0; b < 2048; ++b) {
+      const double e = (double)(b - 1023);
+      ebt[2 * b] = e * c->t.math.ln2_hi;  // exact: 21 significant bits times 11
+      ebt[2 * b + 1] = e * c->t.math.ln2_lo;
+    }
+    const double* ebd = nullptr;
+    if ((st = upload(c, ebt, &ebd)) != FSBM_OK) return bail(st);
+    c->t.math.etab = reinterpret_cast<const double2*>(ebd);
     c->t.math.l256_hi = hi / 256.0;
     c->t.math.l256_lo = c->t.math.ln2_lo / 256.0;
     c->t.math.inv_l256 = (double)(256.0L / ln2);
@@ -462,8 +492,31 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
   }
   std::stable_sort(cls.begin(), cls.end(), [](const Cls& a, const Cls& b) { return a.cost > b.cost; });
   std::memset(c->t.bucket_rank, -1, sizeof(c->t.bucket_rank));
-  for (size_t r = 0; r < cls.size(); ++r) c->t.bucket_rank[cls[r].g * (kMaxSpecies + 1) + cls[r].ns] = (int8_t)r;
+  std::memset(c->t.rank_cost, 0, sizeof(c->t.rank_cost));
+  for (size_t r = 0; r < cls.size(); ++r) {
+    c->t.bucket_rank[cls[r].g * (kMaxSpecies + 1) + cls[r].ns] = (int8_t)r;
+    c->t.rank_cost[r] = (int64_t)cls[r].cost;  // an integer below 2^53: exact
+  }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(FSBM_E_CUDA);
+  *out = c;
+  return FSBM_OK;
+}
+
+fsbm_status fsbm_coal_clone(const fsbm_coal_ctx* src, void* stream, fsbm_coal_ctx** out) {
+  if (!out) return FSBM_E_ARG;
+  *out = nullptr;
+  if (!src) return FSBM_E_ARG;
+  fsbm_coal_ctx* c = new fsbm_coal_ctx();
+  c->S = src->S;
+  c->G = src->G;
+  c->precision = src->precision;
+  c->device = src->device;
+  c->n_sms = src->n_sms;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->t = src->t;            // device pointers into the shared tables
+  c->tables = src->tables;  // one more holder
+  c->block_dim = src->block_dim;
+  c->plan_valid = false;    // planned again on the replica's first step (no allocation)
   *out = c;
   return FSBM_OK;
 }
@@ -476,10 +529,35 @@ fsbm_status fsbm_coal_step(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n
   return run_step(c, to_dev(s), n_points, dt, n_steps);
 }
 
+fsbm_status fsbm_coal_step_shard(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt,
+                                 int32_t n_steps, int32_t shard, int32_t n_shards) {
+  if (!c) return FSBM_E_ARG;
+  fsbm_status st = check_state(c, s, n_points, dt, n_steps, "fsbm_coal_step_shard");
+  if (st != FSBM_OK) return st;
+  if (n_shards < 1 || n_shards > kMaxShards || shard < 0 || shard >= n_shards)
+    return fail(c, FSBM_E_ARG, "fsbm_coal_step_shard: need 0 <= shard < n_shards <= 1024");
+  return run_step(c, to_dev(s), n_points, dt, n_steps, shard, n_shards);
+}
+
+fsbm_status fsbm_coal_shard_bounds(const int64_t* run_count, const int64_t* run_cost, int32_t n_runs,
+                                   int32_t n_shards, int64_t* bounds) {
+  if (n_runs < 0 || (n_runs > 0 && (!run_count || !run_cost)) || n_shards < 1 || n_shards > kMaxShards || !bounds)
+    return FSBM_E_ARG;
+  int64_t T = 0;
+  for (int r = 0; r < n_runs; ++r) {
+    if (run_count[r] < 0 || run_cost[r] < 0) return FSBM_E_ARG;
+    if (run_cost[r] > 0 && run_count[r] > ((int64_t)1 << 62) / n_shards / run_cost[r]) return FSBM_E_ARG;
+    T += run_count[r] * run_cost[r];
+    if (T > ((int64_t)1 << 62) / n_shards) return FSBM_E_ARG;
+  }
+  for (int q = 0; q <= n_shards; ++q) bounds[q] = shard_bound(run_count, run_cost, n_runs, n_shards, q);
+  return FSBM_OK;
+}
+
 fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int64_t n_points, double dt,
                                 int32_t n_steps) {
   if (!c) return FSBM_E_ARG;
-  fsbm_status st = check_state(c, h, n_points, dt, n_steps);
+  fsbm_status st = check_state(c, h, n_points, dt, n_steps, "fsbm_coal_step_host");
   if (st != FSBM_OK) return st;
   if (n_points == 0) return FSBM_OK;
   const size_t esz = c->precision == FSBM_FP64 ? sizeof(double) : sizeof(float);
@@ -655,7 +733,7 @@ fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* c, const fsbm_wrf_state* w, double
 
 fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points) {
   if (!c) return FSBM_E_ARG;
-  fsbm_status st = check_state(c, s, n_points, 1.0, 1);
+  fsbm_status st = check_state(c, s, n_points, 1.0, 1, "fsbm_coal_autotune");
   if (st != FSBM_OK) return st;
   if (n_points == 0) return FSBM_OK;
   // A sample of up to 2^18 points runs 3 collision steps per candidate: long enough that the
@@ -769,10 +847,12 @@ fsbm_status fsbm_coal_get_stats(fsbm_coal_ctx* c, fsbm_coal_stats* out) {
     }
     lst->clear();
   }
-  int32_t cnt[2] = {0, 0};
+  int32_t cnt[4] = {0, 0, 0, 0};
   if (c->scratch.counters) CU(c, cudaMemcpy(cnt, c->scratch.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
   out->n_points = c->last_n;
   out->n_active = cnt[0];
+  out->shard_begin = cnt[3];
+  out->shard_end = cnt[2];
   out->block_dim = c->plan.block_dim;
   out->grid_dim = c->plan.grid_dim;
   out->graph_replayed = c->last_replayed ? 1 : 0;
@@ -797,7 +877,7 @@ fsbm_status fsbm_coal_destroy(fsbm_coal_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  for (void* p : c->table_allocs) cudaFree(p);
+  c->tables.reset();  // freed here unless a replica still holds them
   if (c->scratch.block_counts) cudaFree(c->scratch.block_counts);
   if (c->scratch.active_list) cudaFree(c->scratch.active_list);
   if (c->scratch.counters) cudaFree(c->scratch.counters);
@@ -861,7 +941,7 @@ int32_t* g_noalloc_addr[kNoAllocMaxDevices] = {};
 extern "C" fsbm_status fsbm_coal_step_noalloc(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points,
                                               double dt, int32_t n_steps) {
   if (!c) return FSBM_E_ARG;
-  fsbm_status st = check_state(c, s, n_points, dt, n_steps);
+  fsbm_status st = check_state(c, s, n_points, dt, n_steps, "fsbm_coal_step_noalloc");
   if (st != FSBM_OK) return st;
   if (n_points > kNoAllocMaxPoints)
     return fail(c, FSBM_E_ARG,

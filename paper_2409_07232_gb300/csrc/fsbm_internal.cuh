@@ -5,12 +5,13 @@
 //                     d = |i - j|: on a geometric grid x_k = x0 alpha^k the pair's mass
 //                     x_i + x_j = x_max (1 + alpha^-d) lands in bin max(i,j) + kappa[d]
 //                     with c = ((1 + alpha^-d) alpha^-kappa - 1) / (alpha - 1), so both
-//                     depend on d only (the pair tables of Sec. V-A shrink to length n).
+//                     depend on d only (the pair tables of Sec. VI-A shrink to length n).
 //   x[k]              bin masses.
-//   Kd[d][m][s*S+l]   kernel of species s bin m-d with species l bin m (halved for the
-//                     same-species diagonal d = 0, s = l, which counts once), the S*S ordered
-//                     species pairs innermost: the gain pass puts one lane per species
-//                     orientation on the same (d, m), so a warp's loads are contiguous.
+//   Kd[d][m][s*S+l]   kernel of species s bin m-d with species l bin m times
+//                     1 + alpha^-d = (x_{m-d} + x_m) / x_m (halved for the same-species
+//                     diagonal d = 0, s = l, which counts once), the S*S ordered species pairs
+//                     innermost: the gain pass puts one lane per species orientation on the
+//                     same (d, m), so a warp's loads are contiguous.
 //   Kr[a][b][j][i]    kernel of species a bin i with species b bin j (i fastest): the
 //                     layout of the loss mat-vec, one lane per row i.
 #pragma once
@@ -60,6 +61,7 @@ struct GridDev {
 struct Tables {
   int S;
   int G;
+  int64_t rank_cost[kMaxGrids * kMaxSpecies];  // bin pairs per step of a point of each LPT rank
   int mode;                       // 0 pairwise (Jacobi), 1 SWEEP (Bott's in-place order, FP64)
   int levels;                     // 1: kernels at two pressure levels (per-point weight)
   double p1, p2;                  // their pressures, hPa
@@ -97,15 +99,47 @@ __device__ __forceinline__ double level_weight(const Tables& t, const PointsDev&
 struct Scratch {
   int32_t* block_counts;   // [kNumBuckets][n_blocks]
   int32_t* active_list;    // [n_points]
-  int32_t* counters;       // [0] active count, [1] queue head
+  int32_t* counters;       // [0] active count, [1] queue head, [2] end of the list part this
+                           // call steps, [3] its start
   int64_t n_blocks;
 };
 
+constexpr int kMaxShards = 1024;
+
+// Equal-cost contiguous shards of a cost-ordered list. Grid points are independent (Sec. VI-A),
+// so a list split into contiguous parts needs no exchange between the parts. The list is n_runs
+// runs; run r holds cnt[r] entries of cost cost[r] >= 0 each. With T the total cost, bound q of
+// W (q = 0..W) is the first position whose cost prefix reaches ceil(q T / W) (bound 0 is 0,
+// bound W the entry count), so every shard's cost lies within one entry's cost (plus one) of
+// T / W. Integer arithmetic only: the same bounds on the host and on the device. Callers keep
+// W <= kMaxShards and T below 2^62 / W.
+__host__ __device__ inline int64_t shard_bound(const int64_t* cnt, const int64_t* cost, int n_runs, int W, int q) {
+  int64_t T = 0, N = 0;
+  for (int r = 0; r < n_runs; ++r) {
+    T += cnt[r] * cost[r];
+    N += cnt[r];
+  }
+  if (q <= 0) return 0;
+  if (q >= W) return N;
+  const int64_t target = ((int64_t)q * T + W - 1) / W;
+  int64_t pos = 0, pre = 0;
+  for (int r = 0; r < n_runs; ++r) {
+    const int64_t run = cnt[r] * cost[r];
+    if (pre + run >= target) {
+      const int64_t need = target - pre;
+      return pos + (need > 0 ? (need + cost[r] - 1) / cost[r] : 0);  // need > 0 implies cost[r] > 0
+    }
+    pre += run;
+    pos += cnt[r];
+  }
+  return N;
+}
+
 constexpr int kCompactThreads = 256;
 
-// compact.cu
+// compact.cu: classify, order, and (n_shards > 1) keep shard `shard` of the ordered list
 cudaError_t launch_compact(const Tables& t, const PointsDev& p, int64_t n_points, const Scratch& s,
-                           cudaStream_t stream);
+                           cudaStream_t stream, int shard = 0, int n_shards = 1);
 
 // coal_kernel.cu
 struct CoalLaunch {

@@ -15,8 +15,9 @@
 // checked against CUDA's log/exp/expm1 by fsbm_coal_math_check.
 //
 // Tables (built on the host in extended precision, rounded to FP64, copied to the device once
-// per context), both read as one 16-byte load per call:
+// per context), each read as one 16-byte load per call:
 //   logtab[j] = (1 / F_j, ln F_j) for F_j = 1 + j/512, j = 0..512
+//   etab[b]   = (e ln2_hi, e ln2_lo) for e = b - 1023, b = 0..2047 (e ln2_hi exact)
 //   exptab[j] = (hi, lo) with hi + lo = 2^(j/256), j = 0..255 (lo: the rounding error of hi)
 #pragma once
 #include <cstdint>
@@ -32,6 +33,7 @@ constexpr int kExpTab = 256;
 struct MathTabs {
   const double2* logtab;   // [kLogTab]
   const double2* exptab;   // [kExpTab]
+  const double2* etab;     // [2048] (e ln2_hi, e ln2_lo) for the biased exponent e + 1023
   double ln2_hi, ln2_lo;   // ln 2 = hi + lo
   double l256_hi, l256_lo; // (ln 2) / 256 = hi + lo (the above divided by 256, exactly)
   double inv_l256;         // 256 / ln 2
@@ -41,11 +43,12 @@ struct MathTabs {
 // ln x for normal x > 0 (callers guarantee x >= 1e-300), absolute error about 2e-16 plus the
 // rounding of the result. x = 2^e m with m in [1, 2); F = 1 + j/512 is the table point
 // nearest m, built from the index bits (so m - F is exact, |m - F| <= 2^-10) and
-// ln x = e ln2 + ln F + ln(1 + u) with u = (m - F) / F, |u| <= 2^-10.
+// ln x = e ln2 + ln F + ln(1 + u) with u = (m - F) / F, |u| <= 2^-10. e ln2 comes from a
+// table indexed by the exponent bits (a load instead of an integer-to-FP64 conversion,
+// which would take an FP64-pipe slot).
 __device__ __forceinline__ double fsbm_log(double x, const MathTabs& mt) {
   const int hi = __double2hiint(x);
   const int lo = __double2loint(x);
-  const int e = (hi >> 20) - 1023;
   const int mb = hi & 0x000fffff;
   const int j = (mb + 0x400) >> 11;                         // nearest j / 512, in [0, 512]
   const double m = __hiloint2double(mb | 0x3ff00000, lo);   // in [1, 2)
@@ -56,8 +59,8 @@ __device__ __forceinline__ double fsbm_log(double x, const MathTabs& mt) {
   double q = fma(u, -0.25, 1.0 / 3.0);
   q = fma(q, u, -0.5);
   const double lp = fma(u * u, q, u);
-  const double de = (double)e;
-  return fma(de, mt.ln2_hi, t.y) + fma(de, mt.ln2_lo, lp);
+  const double2 te = __ldg(mt.etab + (hi >> 20));
+  return (te.x + t.y) + (te.y + lp);
 }
 
 // e^y (*ex) and e^y - 1 (*em1) for |y| <= 700, from one reduction:

@@ -4,7 +4,7 @@
 // spectrum its predecessors left (Bott 1998; the routine the paper ports is coal_bott_new,
 // Sec. III, Listing 1). The result depends on the visiting order, so there is no parallelism
 // inside a point: this kernel gives each grid point one thread, which is the paper's own
-// mapping of the collision loop (one OpenMP-offload thread per point, Sec. V-B, Listing 6).
+// mapping of the collision loop (one OpenMP-offload thread per point, Sec. VI-B, Listing 6).
 // It is the cross-check form next to the pairwise kernel; it runs in FP64 only.
 //
 // Per point and step, in this order:
@@ -51,9 +51,9 @@ __device__ __forceinline__ double sweep_flux(double dM, double g_k, double M_k1,
 
 __global__ void k_sweep(Tables t, PointsDev pd, const int32_t* __restrict__ list, const int32_t* counters,
                         double dt, int n_steps) {
-  const int n_active = counters[0];
+  const int q0 = counters[1], q1 = counters[2];  // the list part this call steps
   const int S = t.S;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_active; q += gridDim.x * blockDim.x) {
+  for (int q = q0 + blockIdx.x * blockDim.x + threadIdx.x; q < q1; q += gridDim.x * blockDim.x) {
     const int p = list[q];
     const GridDev& G = t.g[pd.grid_id[p]];
     const int n = G.n;

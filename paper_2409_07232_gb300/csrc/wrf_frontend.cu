@@ -3,7 +3,7 @@
 // WRF keeps a patch's fields over memory ranges (ims:ime, kms:kme, jms:jme), i fastest, and a
 // thread works on a tile inside them (Sec. I); FSBM keeps one such array per species with the
 // bin as the last index. The collision step runs at the tile points that pass the loop's tests
-// (Sec. III, Listing 1) and the predicate kept from the loop fission (Sec. V-B, Listing 5).
+// (Sec. III, Listing 1) and the predicate kept from the loop fission (Sec. VI-B, Listing 6).
 // These kernels move the tile into the packed point layout the collision kernels read (one
 // fixed slot of ns x n values per tile point, so no prefix sum is needed; only the slots of
 // points that will be stepped are filled) and write the stepped points back.

@@ -5,7 +5,7 @@ per-point bin spectra, cloud masks and temperatures. Nothing here applies the co
 step. Both the CPU oracle and the CUDA library consume these arrays unchanged.
 
 The paper's test case is WRF's CONUS-12km thunderstorm run (425 x 300 x 50 points,
-dt = 5 s; Sec. IV), whose data and FSBM's tabulated kernels (Sec. V-A, Listing 2) are not
+dt = 5 s; Sec. IV), whose data and FSBM's tabulated kernels (Sec. VI-A, Listing 3) are not
 available. The recipes below stand in for them with the same shapes:
 
 * grid s: n = 33 s mass bins, x_k = x0 * 2^(k/s), x0 = mass of a 2 um water sphere

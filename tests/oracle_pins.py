@@ -326,7 +326,7 @@ def pin_sweep_caps_empty_exactly(orc):
 
 
 def pin_pressure_levels(orc):
-    """Kernels at two pressure levels (Sec. V-A, Listing 2: each collision table is formed from
+    """Kernels at two pressure levels (Sec. VI-A, Listing 3: each collision table is formed from
     a 750 mb and a 500 mb table; the reading: linear in pressure between them, constant
     outside). Checked without the interpolation formula: a point at or beyond 750 mb steps
     exactly as with the 750 mb table alone, one at or beyond 500 mb as with the 500 mb table

@@ -4,6 +4,7 @@ import pytest
 
 import synth
 import paper_2409_07232_gb300 as pkg
+from compaction_order import expected_active_order
 from gpu_helpers import assert_parity, run_gpu, run_oracle
 from synth.workloads import sphere_mass
 
@@ -115,35 +116,12 @@ def test_same_species_reads_upper_triangle():
     assert_parity(w, got, out, ref, ref_out, pkg.FSBM_FP64)
 
 
-def _expected_active_order(w):
-    """Independent restatement of the compaction rule: points that pass the metadata checks,
-    costliest (grid, stored-species) class first by pair count n(n+1)/2 ns + ns(ns-1)/2 n^2
-    (ties: lower grid, then fewer species), ascending point index inside a class."""
-    S = w.n_species
-    classes = []
-    for g, n in enumerate(w.bins_per_grid):
-        for ns in range(1, S + 1):
-            classes.append((-(ns * n * (n + 1) / 2 + ns * (ns - 1) / 2 * n * n), g, ns))
-    rank = {(g, ns): r for r, (_, g, ns) in enumerate(sorted(classes, key=lambda c: c[0]))}
-    keyed = []
-    for p in range(w.n_points):
-        if w.cloudy is not None and w.cloudy[p] == 0:
-            continue
-        if w.temperature is not None and not (float(w.temperature[p]) > w.t_min_K):
-            continue
-        ns = bin(int(w.species_mask[p])).count("1")
-        if ns == 0:
-            continue
-        keyed.append((rank[(int(w.grid_id[p]), ns)], p))
-    return np.array([p for _, p in sorted(keyed)], np.int32)
-
-
 def test_compaction_order_is_exact():
     w = synth.config4(n_points=3000, seed=31)
     rng = np.random.default_rng(1)
     w.cloudy = (rng.random(w.n_points) > 0.3).astype(np.uint8)
     w.temperature = rng.uniform(200, 300, w.n_points).astype(np.float32)
-    exp = _expected_active_order(w)
+    exp = expected_active_order(w)
     with pkg.FsbmCoal(w.cfg(), precision=pkg.FSBM_FP32_SPLIT) as fc:
         ds = fc.upload(w.state())
         fc.step(ds, w.dt, 1)

@@ -1,8 +1,8 @@
-"""Collection kernels at two pressure levels (Sec. V-A, Listing 2: every FSBM collision table is
+"""Collection kernels at two pressure levels (Sec. VI-A, Listing 3: every FSBM collision table is
 formed from a 750 mb and a 500 mb table), GPU against the oracle through the C ABI.
 
 A point at pressure p collides with K1 + w (K2 - K1), w = (p1 - p) / (p1 - p2) clamped to
-[0, 1]. The GPU reads both tables on demand per pair (Listing 4) as K1 + w D with the
+[0, 1]. The GPU reads both tables on demand per pair (Listing 5) as K1 + w D with the
 difference table D = K2 - K1. Tolerances are the parity bounds of the two forms (1e-12 and 1e-5
 relative L1 per point): the GPU's fused multiply-add and its precomputed D differ from the
 oracle's K1 + w (K2 - K1) by a rounding per entry.

@@ -3,7 +3,7 @@
 WRF keeps a patch's fields over memory ranges with i fastest and works on a tile inside them
 (Sec. I); FSBM holds one array per species with the bin last; the collision step runs at tile
 points warmer than 223.15 K (Sec. III, Listing 1) where the fission's predicate array says so
-(Sec. V-B, Listing 5). The test lays the points of a CONUS-shaped sample out in such arrays
+(Sec. VI-B, Listing 6). The test lays the points of a CONUS-shaped sample out in such arrays
 (1-based Fortran ranges, a tile strictly inside the memory ranges, some points cold, some with
 the predicate off), steps them through the front end, and compares every tile point with the
 same points stepped through fsbm_coal_step (bitwise: the same kernels run on the same values)

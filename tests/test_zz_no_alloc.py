@@ -52,3 +52,42 @@ def test_noalloc_refuses_batches_above_its_capacity():
         assert "262144" in pkg.fsbm_coal_last_error(fc.ctx)
         got, _ = fc.download(ds)
         assert np.array_equal(got, before.cpu().numpy())
+
+
+def test_noalloc_alone_on_a_fresh_context_allocates_nothing():
+    """A context whose only steps are fsbm_coal_step_noalloc, at exactly the fixed capacity of
+    262144 points (every part of the fixed array in use): two calls in a row, the device's free
+    memory unchanged around the second (the first may load the library's device code), and the
+    spectra equal to fsbm_coal_step's on the same points within the FP64 parity tolerance."""
+    import torch
+    w = synth.config1(n_points=262144, seed=4343)
+    w.n_steps = 2
+    with pkg.FsbmCoal(w.cfg(), precision=pkg.FSBM_FP64) as fc:
+        b = fc.upload(w.state())
+        pkg.binding.fsbm_coal_step_noalloc(fc.ctx, b.struct, b.n_points, w.dt, w.n_steps)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        pkg.binding.fsbm_coal_step_noalloc(fc.ctx, b.struct, b.n_points, w.dt, w.n_steps)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        gb, ob = fc.download(b)
+    assert abs(free1 - free0) < (2 << 20), (free0, free1)
+    with pkg.FsbmCoal(w.cfg(), precision=pkg.FSBM_FP64) as fc:
+        a = fc.upload(w.state())
+        for _ in range(2):
+            fc.step(a, w.dt, w.n_steps)
+        ga, oa = fc.download(a)
+    n = w.bins_per_grid[0]                                    # one grid, one species: [point][bin]
+    err = np.abs(gb - ga).reshape(-1, n).sum(axis=1) / np.abs(ga).reshape(-1, n).sum(axis=1)
+    assert err.max() <= TOL[pkg.FSBM_FP64], float(err.max())
+    assert np.array_equal(oa["status"], ob["status"])
+    assert int((ob["status"] & 6 == 0).sum()) == w.n_points   # every point ran
+
+
+def test_noalloc_errors_name_the_entry_point():
+    w = synth.config1(n_points=4)
+    with pkg.FsbmCoal(w.cfg()) as fc:
+        ds = fc.upload(w.state())
+        with pytest.raises(pkg.FsbmError):
+            pkg.binding.fsbm_coal_step_noalloc(fc.ctx, ds.struct, ds.n_points, -1.0, 1)
+        assert pkg.fsbm_coal_last_error(fc.ctx).startswith("fsbm_coal_step_noalloc:")
