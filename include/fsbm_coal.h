@@ -151,7 +151,7 @@ typedef struct {
   int32_t block_dim;            /* threads per CTA of the collision kernel                */
   int32_t grid_dim;             /* persistent CTAs                                        */
   int32_t graph_replayed;       /* 1 if the last step was a CUDA-graph replay             */
-  int32_t reserved;
+  int32_t tune_cache_hit;       /* 1 if the last autotune call took a remembered choice    */
   /* with timing on (fsbm_coal_set_timing), totals since the previous fsbm_coal_get_stats
    * call, measured with CUDA events on the context's stream:                            */
   double coal_ms;               /* collision-kernel time (steps launched without a graph) */
@@ -274,10 +274,19 @@ FSBM_API fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* ctx, const fsbm_wrf_state
                                         int32_t n_steps);
 
 /* Time the collision kernel for each candidate CTA size (32, 64, 128, 256, 512 threads) on a
- * copy of the first 2^18 points of the given device state (all of it if smaller), three
- * collision steps of 5 s each, and keep the fastest for later steps. The caller's spectra are not
- * modified. Synchronous; allocates a temporary copy of the sample. The paper has no
- * counterpart. */
+ * copy of the first 2^16 points of the given device state (all of it if smaller), stepping the
+ * sample n_steps collision steps of dt seconds (the caller's own call shape: the limiter's
+ * firing, and so the cost, depends on dt), and keep the fastest for later steps. The choice is
+ * remembered for the process under a key of the device, precision, mode, kernel levels, bin
+ * grids, species count, range threshold, dt, n_steps and the sample's mix of point classes
+ * (grid and stored-species count, in eighths): a later call with the same key, from this or
+ * another context, takes it without timing (fsbm_coal_get_stats: tune_cache_hit). The caller's
+ * spectra are not modified. Synchronous; allocates a temporary copy of the sample. The paper
+ * has no counterpart. */
+FSBM_API fsbm_status fsbm_coal_autotune_steps(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points,
+                                              double dt, int32_t n_steps);
+
+/* fsbm_coal_autotune_steps with dt = 5 s and 3 steps. */
 FSBM_API fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points);
 
 /* Enable (1) or disable (0, the default) CUDA-graph capture of fsbm_coal_step: the first

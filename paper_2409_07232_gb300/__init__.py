@@ -22,6 +22,7 @@ from .binding import (  # noqa: F401
     FSBM_ST_LIMITED,
     FsbmError,
     fsbm_coal_autotune,
+    fsbm_coal_autotune_steps,
     fsbm_coal_clone,
     fsbm_coal_destroy,
     fsbm_coal_get_active_list,
@@ -149,8 +150,12 @@ class FsbmCoal:
                                     mass_error)
         binding.fsbm_coal_step_wrf(self.ctx, st, dt, n_steps)
 
-    def autotune(self, ds: DeviceState) -> None:
-        fsbm_coal_autotune(self.ctx, ds.struct, ds.n_points)
+    def autotune(self, ds: DeviceState, dt: Optional[float] = None, n_steps: Optional[int] = None) -> None:
+        """Pick the CTA size on a sample of the batch, at the caller's dt and n_steps if given."""
+        if dt is None or n_steps is None:
+            fsbm_coal_autotune(self.ctx, ds.struct, ds.n_points)
+        else:
+            fsbm_coal_autotune_steps(self.ctx, ds.struct, ds.n_points, dt, n_steps)
 
     def set_graph(self, enable: bool) -> None:
         fsbm_coal_set_graph(self.ctx, enable)

@@ -38,7 +38,7 @@ _STATUS_NAMES = {0: "FSBM_OK", -1: "FSBM_E_ARG", -2: "FSBM_E_CUDA", -3: "FSBM_E_
 
 # Every entry point include/fsbm_coal.h declares.
 EXPORTS = ("fsbm_coal_init", "fsbm_coal_clone", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_step_noalloc", "fsbm_coal_step_wrf",
-           "fsbm_coal_step_shard", "fsbm_coal_shard_bounds", "fsbm_coal_autotune",
+           "fsbm_coal_step_shard", "fsbm_coal_shard_bounds", "fsbm_coal_autotune", "fsbm_coal_autotune_steps",
            "fsbm_coal_set_graph", "fsbm_coal_set_block", "fsbm_coal_set_timing", "fsbm_coal_get_stats",
            "fsbm_coal_get_active_list", "fsbm_coal_math_check", "fsbm_coal_destroy", "fsbm_coal_last_error")
 
@@ -107,7 +107,7 @@ class fsbm_coal_stats(ctypes.Structure):
         ("block_dim", ctypes.c_int32),
         ("grid_dim", ctypes.c_int32),
         ("graph_replayed", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("tune_cache_hit", ctypes.c_int32),
         ("coal_ms", ctypes.c_double),
         ("coal_launches", ctypes.c_int64),
         ("step_ms", ctypes.c_double),
@@ -145,6 +145,8 @@ def load(path: str = LIB_PATH):
                                       ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_shard_bounds": ([V, V, ctypes.c_int32, ctypes.c_int32, V], ctypes.c_int),
             "fsbm_coal_autotune": ([V, P(fsbm_coal_state), ctypes.c_int64], ctypes.c_int),
+            "fsbm_coal_autotune_steps": ([V, P(fsbm_coal_state), ctypes.c_int64, ctypes.c_double, ctypes.c_int32],
+                                         ctypes.c_int),
             "fsbm_coal_set_graph": ([V, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_set_block": ([V, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_set_timing": ([V, ctypes.c_int32], ctypes.c_int),
@@ -273,6 +275,11 @@ def fsbm_coal_autotune(ctx, state: fsbm_coal_state, n_points: int) -> None:
     _check(ctx, load().fsbm_coal_autotune(ctx, ctypes.byref(state), int(n_points)), "fsbm_coal_autotune")
 
 
+def fsbm_coal_autotune_steps(ctx, state: fsbm_coal_state, n_points: int, dt: float, n_steps: int) -> None:
+    _check(ctx, load().fsbm_coal_autotune_steps(ctx, ctypes.byref(state), int(n_points), float(dt), int(n_steps)),
+           "fsbm_coal_autotune_steps")
+
+
 def fsbm_coal_set_graph(ctx, enable: bool) -> None:
     _check(ctx, load().fsbm_coal_set_graph(ctx, 1 if enable else 0), "fsbm_coal_set_graph")
 
@@ -288,7 +295,7 @@ def fsbm_coal_set_timing(ctx, enable: bool) -> None:
 def fsbm_coal_get_stats(ctx) -> dict:
     st = fsbm_coal_stats()
     _check(ctx, load().fsbm_coal_get_stats(ctx, ctypes.byref(st)), "fsbm_coal_get_stats")
-    return {name: getattr(st, name) for name, _ in fsbm_coal_stats._fields_ if name != "reserved"}
+    return {name: getattr(st, name) for name, _ in fsbm_coal_stats._fields_}
 
 
 def fsbm_coal_get_active_list(ctx, cap: int) -> np.ndarray:

@@ -60,6 +60,15 @@ __device__ __forceinline__ int warp_max_i(int v) {
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// e / n for 0 <= e < 5 n, 2 <= n <= 512, from the grid's inv_n = floor(2^32 / n) + 1 (exact
+// in that range; an integer division by a value known only at run time costs some twenty
+// instructions)
+__device__ __forceinline__ int div_n(int e, unsigned inv_n) { return (int)__umulhi((unsigned)e, inv_n); }
 
 // Bott's flux of mass dM deposited in bin k toward bin k + 1 (see fsbm_coal.h).
 __device__ __forceinline__ double bott_flux(double dM, double Mk, double Mk1, double c) {
@@ -224,15 +233,14 @@ struct Smem {
   T* lam;         // [S][nmax]
   T* xs;          // [nmax]
   T* cd;          // [nmax] Courant number per bin distance
-  T* llam;        // [S*nmax] the limited rows' ratios, ascending
-  T* lN;          // [S*nmax] their number concentrations, in the same order
+  T* llam;        // [S*nmax] the limited rows' ratios, in row order
+  T* lN;          // [S*nmax] their number concentrations
   int* lim;       // [S*nmax] rows whose limiter ratio is below 1, ascending row index
-  int* loff;      // [S*nmax] Kr offset (species id of the row's slot, bin) of the sorted rows
-  int* rk;        // [S*nmax] position of a limited row in the ratio order
+  int* loff;      // [S*nmax] Kr offset (species id of the row's species, bin) of those rows
   static __host__ __device__ size_t bytes(int nmax, int S) {
     size_t b = sizeof(double) * 2 * S * nmax + sizeof(Sum) * 2 * S * S * nmax;
     if (sizeof(T) != sizeof(double)) b += sizeof(T) * S * nmax;
-    b += sizeof(T) * (4 * S * nmax + 2 * nmax) + sizeof(int) * 3 * S * nmax;
+    b += sizeof(T) * (4 * S * nmax + 2 * nmax) + sizeof(int) * 2 * S * nmax;
     return (b + 15) & ~size_t(15);
   }
   __device__ void carve(unsigned char* base, int nmax, int S) {
@@ -266,8 +274,6 @@ struct Smem {
     lim = reinterpret_cast<int*>(p);
     p += sizeof(int) * S * nmax;
     loff = reinterpret_cast<int*>(p);
-    p += sizeof(int) * S * nmax;
-    rk = reinterpret_cast<int*>(p);
   }
 };
 
@@ -289,8 +295,6 @@ __device__ __forceinline__ double fsbm_rcp(double x) {
   return fma(y, fma(e, e, e), y);
 }
 // Sign tests on the bit pattern run on the integer pipes instead of the (slow) FP64 pipe.
-__device__ __forceinline__ bool pos(double v) { return __double_as_longlong(v) > 0; }  // v > 0, v not NaN-negative
-__device__ __forceinline__ bool pos(float v) { return __float_as_int(v) > 0; }
 __device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
 __device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) << 1) == 0; }
 // min of two non-negative doubles through their bit patterns (they order like integers)
@@ -298,9 +302,6 @@ __device__ __forceinline__ double min_nonneg(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b) ? a : b;
 }
 __device__ __forceinline__ float min_nonneg(float a, float b) { return fminf(a, b); }
-// bit pattern of a non-negative value, ordered like the value
-__device__ __forceinline__ long long ord_bits(double v) { return __double_as_longlong(v); }
-__device__ __forceinline__ int ord_bits(float v) { return __float_as_int(v); }
 // Bott's flux with target-bin constants hoisted out of the pair loop:
 //  * bin k+1 holds at least 1e-43 of the largest content bin k can reach (Mk + 2B): then
 //    1e-60 g is below half an ulp of M_{k+1}, M_{k+1} + 1e-60 g rounds to M_{k+1} exactly, and
@@ -449,14 +450,18 @@ template <typename T>
 struct StoreOf { using type = T; };
 
 // LEV: kernels at two pressure levels (a separate instantiation, so that the one-level kernel
-// keeps its registers and instructions)
+// keeps its registers and instructions). The FP32 form is held to 64 registers (four CTAs of
+// 256 threads per SM): it is bound by instruction issue and latency, and more resident warps
+// hide more of it; the FP64 form is bound by the FP64 pipe and keeps what it needs.
 template <typename T, bool LEV>
-__global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list, int32_t* counters, double dt,
+__global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list, int32_t* counters, double dt,
                        int n_steps, int nmax) {
   using Store = typename StoreOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ Orient ori[kMaxOrient];
+  __shared__ int8_t s_plist[kMaxSpecies][kMaxOrient];  // orientations whose product is slot c
+  __shared__ int s_np[kMaxSpecies];
   __shared__ int s_lo[kMaxSpecies], s_hi[kMaxSpecies], s_sp[kMaxSpecies];
   __shared__ int s_next;
   __shared__ int s_task;
@@ -542,6 +547,11 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
           ori[q++] = Orient{(int8_t)a, (int8_t)b, 0, (int8_t)cs, ia * S + ib};
           if (a != b) ori[q++] = Orient{(int8_t)b, (int8_t)a, 1, (int8_t)cs, ib * S + ia};
         }
+      for (int c = 0; c < ns; ++c) s_np[c] = 0;
+      for (int o = 0; o < q; ++o) {  // ascending orientation order within every product slot
+        const int c = ori[o].c;
+        s_plist[c][s_np[c]++] = (int8_t)o;
+      }
     }
     __syncthreads();
     const int O = ns * ns;
@@ -553,15 +563,17 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
       //    step ends rescaled to it (the start-of-step total equals B0 to rounding).
       const double Bs = B0;
       for (int a = warp; a < ns; a += nw) {
-        const double* Ma = sm.M + a * n;
-        double mx = 0.0;
-        for (int k = lane; k < n; k += 32) mx = fmax(mx, Ma[k]);
-        mx = warp_max(mx);
-        const double thr = t.tau * mx;
+        // non-negative doubles order like their bit patterns: the largest bin and the range
+        // tests run on the integer pipes (a -0.0 left by the clamp reads as negative: empty)
+        const long long* Ma = reinterpret_cast<const long long*>(sm.M + a * n);
+        long long mx = 0;
+        for (int k = lane; k < n; k += 32) mx = max(mx, Ma[k]);
+        mx = warp_max_ll(mx);
+        long long thr = 1;  // M > 0
+        if (t.tau > 0.0) thr = max(thr, __double_as_longlong(t.tau * __longlong_as_double(mx)));
         int lo = n, hi = -1;
         for (int k = lane; k < n; k += 32) {
-          const double v = Ma[k];
-          if (v > 0.0 && v >= thr) {
+          if (Ma[k] >= thr) {
             lo = min(lo, k);
             hi = max(hi, k);
           }
@@ -574,39 +586,56 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
         }
       }
       for (int e = tid; e < E; e += NT) {
-        const int k = e % n;
+        const int k = e - div_n(e, G.inv_n) * n;
         const T m = (T)sm.M[e];
         sm.N[e] = m * __ldg(Sel<T>::invx(G) + k);  // N = M / x through the table of 1 / x
         if (sizeof(T) != sizeof(double)) sm.Mt[e] = m;
       }
       __syncthreads();
 
-      // 2. requested loss R and limiter ratios (one lane per row (a, i); Kr is i-fastest)
+      // 2. requested loss R and limiter ratios (one lane per row (a, i); Kr is i-fastest, so
+      //    a warp's loads of one column are contiguous). Each lane keeps four partial sums
+      //    (columns j, j+1, j+2, j+3) so that four loads are in flight at once; the partials
+      //    are added in a fixed order.
       const T* __restrict__ Kr = Sel<T>::Kr(G);
+      const T* __restrict__ Krd = lev ? Sel<T>::Kr_d(G) : nullptr;
       bool fired = false;
       for (int r = tid; r < E; r += NT) {
-        const int a = r / n, i = r - a * n;
+        const int a = div_n(r, G.inv_n), i = r - a * n;
         double R = 0.0;
         double lamd = 1.0;
         if (i >= s_lo[a] && i <= s_hi[a]) {
           Acc<T> acc;
           for (int b = 0; b < ns; ++b) {
-            const T* Kab = Kr + (size_t)(s_sp[a] * S + s_sp[b]) * n * n + i;
-            const T* Nb = sm.N + b * n;
-            if (lev) {
-              const T* Kabd = Sel<T>::Kr_d(G) + (size_t)(s_sp[a] * S + s_sp[b]) * n * n + i;
-              for (int j0 = s_lo[b]; j0 <= s_hi[b]; j0 += kLossRun) {
-                const int j1 = min(s_hi[b], j0 + kLossRun - 1);
-                for (int j = j0; j <= j1; ++j)
-                  acc.add(fma(wT, __ldg(Kabd + (size_t)j * n), __ldg(Kab + (size_t)j * n)) * Nb[j]);
-                acc.flush();
+            const size_t base = (size_t)(s_sp[a] * S + s_sp[b]) * n * n + i;
+            const T* __restrict__ Kab = Kr + base;
+            const T* __restrict__ Kabd = lev ? Krd + base : nullptr;
+            const T* __restrict__ Nb = sm.N + b * n;
+            for (int j0 = s_lo[b]; j0 <= s_hi[b]; j0 += kLossRun) {
+              const int j1 = min(s_hi[b], j0 + kLossRun - 1);
+              T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+              int j = j0;
+              for (; j + 3 <= j1; j += 4) {
+                T k0 = __ldg(Kab + (size_t)j * n), k1 = __ldg(Kab + (size_t)(j + 1) * n);
+                T k2 = __ldg(Kab + (size_t)(j + 2) * n), k3 = __ldg(Kab + (size_t)(j + 3) * n);
+                if (lev) {
+                  k0 = fma(wT, __ldg(Kabd + (size_t)j * n), k0);
+                  k1 = fma(wT, __ldg(Kabd + (size_t)(j + 1) * n), k1);
+                  k2 = fma(wT, __ldg(Kabd + (size_t)(j + 2) * n), k2);
+                  k3 = fma(wT, __ldg(Kabd + (size_t)(j + 3) * n), k3);
+                }
+                p0 = fma(k0, Nb[j], p0);
+                p1 = fma(k1, Nb[j + 1], p1);
+                p2 = fma(k2, Nb[j + 2], p2);
+                p3 = fma(k3, Nb[j + 3], p3);
               }
-            } else {
-              for (int j0 = s_lo[b]; j0 <= s_hi[b]; j0 += kLossRun) {
-                const int j1 = min(s_hi[b], j0 + kLossRun - 1);
-                for (int j = j0; j <= j1; ++j) acc.add(__ldg(Kab + (size_t)j * n) * Nb[j]);
-                acc.flush();
+              for (; j <= j1; ++j) {
+                T k0 = __ldg(Kab + (size_t)j * n);
+                if (lev) k0 = fma(wT, __ldg(Kabd + (size_t)j * n), k0);
+                p0 = fma(k0, Nb[j], p0);
               }
+              acc.add((p0 + p1) + (p2 + p3));
+              acc.flush();
             }
           }
           R = dt * sm.M[r] * Num<T>::val(acc.sum());
@@ -623,10 +652,10 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
       if (limited) status |= 1;
 
       // 3. limited losses: loss_i = dt M_i sum_j K N_j min(lam_i, lam_j)
-      //      = lam_i R_i - dt M_i sum_{j: lam_j < lam_i} (lam_i - lam_j) K N_j,
-      //    where lam_i R_i = M_i when lam_i < 1. The correction runs only over the rows whose
-      //    ratio fired, sorted by ratio (ties by row, a fixed order): a row then walks the
-      //    prefix of rows with smaller ratios, with no test per entry.
+      //      = lam_i R_i + dt M_i sum_{j limited} K N_j (min(lam_i, lam_j) - lam_i),
+      //    where lam_i R_i = M_i when lam_i < 1 and every term with lam_j >= lam_i is 0. The
+      //    sum runs over the rows whose ratio fired, gathered once in row order; each row
+      //    walks that list with four partial sums, added in a fixed order.
       if (limited) {
         if (warp == 0) {
           int cnt = 0;
@@ -641,42 +670,49 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
         }
         __syncthreads();
         const int L = s_nlim;
-        for (int q = tid; q < L; q += NT) {  // rank by counting; every entry reads the same list
+        for (int q = tid; q < L; q += NT) {
           const int r = sm.lim[q];
-          const T l = sm.lam[r];
-          // ratios are positive: their bit patterns order like integers (no FP64 compares)
-          const auto lb = ord_bits(l);
-          int rank = 0;
-          for (int q2 = 0; q2 < L; ++q2) {
-            const auto l2b = ord_bits(sm.lam[sm.lim[q2]]);
-            rank += (l2b < lb) || (l2b == lb && q2 < q);
-          }
-          const int b = r / n, j = r - b * n;
-          sm.llam[rank] = l;
-          sm.lN[rank] = sm.N[r];
-          sm.loff[rank] = (s_sp[b] * n + j) * n;
-          sm.rk[r] = rank;
+          const int b = div_n(r, G.inv_n), j = r - b * n;
+          sm.llam[q] = sm.lam[r];
+          sm.lN[q] = sm.N[r];
+          sm.loff[q] = (s_sp[b] * n + j) * n;
         }
         __syncthreads();
         for (int r = tid; r < E; r += NT) {
-          const int a = r / n, i = r - a * n;
+          const int a = div_n(r, G.inv_n), i = r - a * n;
           if (i < s_lo[a] || i > s_hi[a]) continue;
           const T li = sm.lam[r];
-          const int cnt = li < T(1) ? sm.rk[r] : L;  // rows sorted before r have ratios <= lam_i
           const T* __restrict__ Kri = Kr + (size_t)s_sp[a] * S * n * n + i;
-          const T* __restrict__ Krid = lev ? Sel<T>::Kr_d(G) + (size_t)s_sp[a] * S * n * n + i : nullptr;
+          const T* __restrict__ Krid = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
           Acc<T> acc;
-          for (int q0 = 0; q0 < cnt; q0 += kLossRun) {
-            const int q1 = min(cnt, q0 + kLossRun);
-            for (int q = q0; q < q1; ++q) {
-              T Kv = __ldg(Kri + sm.loff[q]);
-              if (lev) Kv = fma(wT, __ldg(Krid + sm.loff[q]), Kv);
-              acc.add((li - sm.llam[q]) * Kv * sm.lN[q]);  // equal ratios add exactly 0
+          for (int q0 = 0; q0 < L; q0 += kLossRun) {
+            const int q1 = min(L, q0 + kLossRun);
+            T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+            int q = q0;
+            for (; q + 3 < q1; q += 4) {
+              T k0 = __ldg(Kri + sm.loff[q]), k1 = __ldg(Kri + sm.loff[q + 1]);
+              T k2 = __ldg(Kri + sm.loff[q + 2]), k3 = __ldg(Kri + sm.loff[q + 3]);
+              if (lev) {
+                k0 = fma(wT, __ldg(Krid + sm.loff[q]), k0);
+                k1 = fma(wT, __ldg(Krid + sm.loff[q + 1]), k1);
+                k2 = fma(wT, __ldg(Krid + sm.loff[q + 2]), k2);
+                k3 = fma(wT, __ldg(Krid + sm.loff[q + 3]), k3);
+              }
+              p0 = fma((min_nonneg(li, sm.llam[q]) - li) * k0, sm.lN[q], p0);
+              p1 = fma((min_nonneg(li, sm.llam[q + 1]) - li) * k1, sm.lN[q + 1], p1);
+              p2 = fma((min_nonneg(li, sm.llam[q + 2]) - li) * k2, sm.lN[q + 2], p2);
+              p3 = fma((min_nonneg(li, sm.llam[q + 3]) - li) * k3, sm.lN[q + 3], p3);
             }
+            for (; q < q1; ++q) {
+              T k0 = __ldg(Kri + sm.loff[q]);
+              if (lev) k0 = fma(wT, __ldg(Krid + sm.loff[q]), k0);
+              p0 = fma((min_nonneg(li, sm.llam[q]) - li) * k0, sm.lN[q], p0);
+            }
+            acc.add((p0 + p1) + (p2 + p3));
             acc.flush();
           }
           const double base = li < T(1) ? sm.M[r] : sm.loss[r];
-          sm.loss[r] = base - dt * sm.M[r] * Num<T>::val(acc.sum());
+          sm.loss[r] = base + dt * sm.M[r] * Num<T>::val(acc.sum());
         }
       }
 
@@ -746,10 +782,10 @@ __global__ void k_coal(Tables t, PointsDev pd, const int32_t* __restrict__ list,
       // 5. update, mass error, clamp, renormalise (FP64). The pre-clamp values go to `loss`
       //    (no longer needed) so that one warp forms both totals in a fixed order.
       for (int e = tid; e < E; e += NT) {
-        const int c = e / n, k = e - c * n;
+        const int c = div_n(e, G.inv_n), k = e - c * n;
         typename Num<T>::Sum gsum = Num<T>::zero();
-        for (int q = 0; q < O; ++q) {
-          if (ori[q].c != c) continue;
+        for (int qq = 0; qq < s_np[c]; ++qq) {
+          const int q = s_plist[c][qq];
           Num<T>::add(gsum, sm.stay[q * n + k]);
           if (k > 0) Num<T>::add(gsum, sm.up[q * n + k - 1]);
         }

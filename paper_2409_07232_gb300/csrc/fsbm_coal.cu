@@ -6,11 +6,13 @@
 // fsbm_coal_step runs the compaction pass (the predicate array of Sec. VI-B, Listing 6) and
 // the persistent collision kernel on the caller's stream, optionally as a CUDA-graph replay.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -64,6 +66,7 @@ struct fsbm_coal_ctx {
   int g_shard = 0, g_nshards = 1;
   bool last_replayed = false;
   int64_t last_n = 0;
+  int tune_cache_hit = 0;
   // CUDA-event timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -74,6 +77,15 @@ struct fsbm_coal_ctx {
 namespace {
 
 const char* kNullCtxMsg = "fsbm_coal: null context";
+
+// NVTX range around an entry point (and its compaction / collision enqueues), so that a timeline
+// from a profiler shows the library's calls by name. Costs nothing measurable without a tool.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 fsbm_status fail(fsbm_coal_ctx* c, fsbm_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -211,7 +223,11 @@ fsbm_status take_events(fsbm_coal_ctx* c, std::pair<cudaEvent_t, cudaEvent_t>* o
 fsbm_status enqueue(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, double dt, int n_steps,
                     const CoalLaunch& plan, bool capturing, int shard, int n_shards) {
   cudaStream_t stream = capturing ? c->cap_stream : c->stream;
-  CU(c, launch_compact(c->t, p, n_points, c->scratch, stream, shard, n_shards));
+  {
+    NvtxRange r("fsbm_coal compact");
+    CU(c, launch_compact(c->t, p, n_points, c->scratch, stream, shard, n_shards));
+  }
+  NvtxRange r("fsbm_coal collide");
   const bool timed = c->timing && !capturing;
   std::pair<cudaEvent_t, cudaEvent_t> ev{};
   if (timed) {
@@ -302,6 +318,7 @@ fsbm_status launch_step(fsbm_coal_ctx* c, const PointsDev& p, int64_t n_points, 
 extern "C" {
 
 fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_ctx** out) {
+  NvtxRange nvtx_("fsbm_coal_init");
   if (!out) return FSBM_E_ARG;
   *out = nullptr;
   if (!cfg) return FSBM_E_ARG;
@@ -370,6 +387,7 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
 
     GridDev& gd = c->t.g[g];
     gd.n = n;
+    gd.inv_n = (unsigned)((uint64_t(1) << 32) / (uint64_t)n + 1);
     std::vector<int> kap;
     std::vector<double> cd;
     pair_offsets(n, al, kap, cd);
@@ -503,6 +521,7 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
 }
 
 fsbm_status fsbm_coal_clone(const fsbm_coal_ctx* src, void* stream, fsbm_coal_ctx** out) {
+  NvtxRange nvtx_("fsbm_coal_clone");
   if (!out) return FSBM_E_ARG;
   *out = nullptr;
   if (!src) return FSBM_E_ARG;
@@ -523,6 +542,7 @@ fsbm_status fsbm_coal_clone(const fsbm_coal_ctx* src, void* stream, fsbm_coal_ct
 
 fsbm_status fsbm_coal_step(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt,
                            int32_t n_steps) {
+  NvtxRange nvtx_("fsbm_coal_step");
   if (!c) return FSBM_E_ARG;
   fsbm_status st = check_state(c, s, n_points, dt, n_steps);
   if (st != FSBM_OK) return st;
@@ -531,6 +551,7 @@ fsbm_status fsbm_coal_step(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n
 
 fsbm_status fsbm_coal_step_shard(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt,
                                  int32_t n_steps, int32_t shard, int32_t n_shards) {
+  NvtxRange nvtx_("fsbm_coal_step_shard");
   if (!c) return FSBM_E_ARG;
   fsbm_status st = check_state(c, s, n_points, dt, n_steps, "fsbm_coal_step_shard");
   if (st != FSBM_OK) return st;
@@ -556,6 +577,7 @@ fsbm_status fsbm_coal_shard_bounds(const int64_t* run_count, const int64_t* run_
 
 fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int64_t n_points, double dt,
                                 int32_t n_steps) {
+  NvtxRange nvtx_("fsbm_coal_step_host");
   if (!c) return FSBM_E_ARG;
   fsbm_status st = check_state(c, h, n_points, dt, n_steps, "fsbm_coal_step_host");
   if (st != FSBM_OK) return st;
@@ -632,6 +654,7 @@ fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int6
 }
 
 fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* c, const fsbm_wrf_state* w, double dt, int32_t n_steps) {
+  NvtxRange nvtx_("fsbm_coal_step_wrf");
   if (!c) return FSBM_E_ARG;
   if (!w) return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: state is NULL");
   if (!(dt >= 0.0) || !std::isfinite(dt) || n_steps < 0)
@@ -731,15 +754,43 @@ fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* c, const fsbm_wrf_state* w, double
   return FSBM_OK;
 }
 
-fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points) {
-  if (!c) return FSBM_E_ARG;
-  fsbm_status st = check_state(c, s, n_points, 1.0, 1, "fsbm_coal_autotune");
+}  // extern "C"
+
+namespace {
+
+// Launch shapes the autotuner remembers for the process, keyed by everything that changes the
+// kernel's cost: the device, precision, mode, kernel levels, bin grids, species count, range
+// threshold, step length, steps per call, and the sample's mix of point classes (grid and
+// stored-species count, in eighths of the sample).
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;
+
+std::string tune_key(const fsbm_coal_ctx* c, double dt, int n_steps, const int32_t* cls_count, int n_cls, int64_t P) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, c->device);
+  std::string k = std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount) + "|p" +
+                  std::to_string(c->precision) + "|m" + std::to_string(c->t.mode) + "|l" + std::to_string(c->t.levels) +
+                  "|S" + std::to_string(c->S);
+  char buf[64];
+  for (int g = 0; g < c->G; ++g) {
+    std::snprintf(buf, sizeof buf, "|g%d:%d", c->t.g[g].n, c->t.g[g].kappa_max);
+    k += buf;
+  }
+  std::snprintf(buf, sizeof buf, "|tau%.17g|dt%.17g|n%d|", c->t.tau, dt, n_steps);
+  k += buf;
+  for (int r = 0; r < n_cls; ++r) k += std::to_string(P > 0 ? (8 * (int64_t)cls_count[r] + P / 2) / P : 0) + ",";
+  return k;
+}
+
+fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt, int n_steps,
+                        const char* who) {
+  fsbm_status st = check_state(c, s, n_points, dt, n_steps, who);
   if (st != FSBM_OK) return st;
+  c->tune_cache_hit = 0;
   if (n_points == 0) return FSBM_OK;
-  // A sample of up to 2^18 points runs 3 collision steps per candidate: long enough that the
+  // A sample of up to 2^16 points runs the caller's steps per candidate: long enough that the
   // per-point start-up work and the last points' tail weigh about as much as in a real call.
-  const int64_t P = std::min<int64_t>(n_points, 1 << 18);
-  constexpr int kTuneSteps = 3;
+  const int64_t P = std::min<int64_t>(n_points, 1 << 16);
   int64_t off[2];
   CU(c, cudaMemcpyAsync(&off[0], s->offset, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaMemcpyAsync(&off[1], s->offset + P, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
@@ -760,7 +811,37 @@ fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64
     cudaFree(tmp);
     return st;
   }
-  c->scratch.n_blocks = (P + kCompactThreads - 1) / kCompactThreads;
+  const int64_t nblk = (P + kCompactThreads - 1) / kCompactThreads;
+  c->scratch.n_blocks = nblk;
+  // the sample's class mix: first positions of the classes in the ordered list (the scanned
+  // counts' first block of every class) and the active count
+  const int n_cls = c->G * c->S;
+  int32_t first[kNumBuckets + 1] = {};
+  cudaError_t ce = launch_compact(c->t, p, P, c->scratch, c->stream);
+  for (int r = 0; r < n_cls && ce == cudaSuccess; ++r)
+    ce = cudaMemcpyAsync(&first[r], c->scratch.block_counts + (int64_t)r * nblk, sizeof(int32_t),
+                         cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(&first[n_cls], c->scratch.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) {
+    cudaFree(tmp);
+    return cuda_fail(c, ce, who);
+  }
+  int32_t cls_count[kNumBuckets] = {};
+  for (int r = 0; r < n_cls; ++r) cls_count[r] = first[r + 1] - first[r];
+  const std::string key = tune_key(c, dt, n_steps, cls_count, n_cls, P);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      cudaFree(tmp);
+      c->block_dim = it->second;
+      c->plan_valid = false;
+      c->tune_cache_hit = 1;
+      return ensure_plan(c);
+    }
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -777,7 +858,7 @@ fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64
       cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
       launch_compact(c->t, p, P, c->scratch, c->stream);
       cudaEventRecord(e0, c->stream);
-      launch_coal(c->t, c->precision, p, c->scratch, 5.0, kTuneSteps, plan, c->stream);
+      launch_coal(c->t, c->precision, p, c->scratch, dt, n_steps, plan, c->stream);
       cudaEventRecord(e1, c->stream);
       cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -793,10 +874,32 @@ fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64
   cudaEventDestroy(e1);
   const cudaError_t le = cudaGetLastError();
   cudaFree(tmp);
-  if (le != cudaSuccess) return cuda_fail(c, le, "fsbm_coal_autotune");
+  if (le != cudaSuccess) return cuda_fail(c, le, who);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_b;
+  }
   c->block_dim = best_b;
   c->plan_valid = false;
   return ensure_plan(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+fsbm_status fsbm_coal_autotune(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points) {
+  NvtxRange nvtx_("fsbm_coal_autotune");
+  if (!c) return FSBM_E_ARG;
+  return autotune_at(c, s, n_points, 5.0, 3, "fsbm_coal_autotune");
+}
+
+fsbm_status fsbm_coal_autotune_steps(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt,
+                                     int32_t n_steps) {
+  NvtxRange nvtx_("fsbm_coal_autotune_steps");
+  if (!c) return FSBM_E_ARG;
+  if (n_steps < 1) return fail(c, FSBM_E_ARG, "fsbm_coal_autotune_steps: n_steps must be >= 1");
+  return autotune_at(c, s, n_points, dt, n_steps, "fsbm_coal_autotune_steps");
 }
 
 fsbm_status fsbm_coal_set_graph(fsbm_coal_ctx* c, int32_t enable) {
@@ -856,6 +959,7 @@ fsbm_status fsbm_coal_get_stats(fsbm_coal_ctx* c, fsbm_coal_stats* out) {
   out->block_dim = c->plan.block_dim;
   out->grid_dim = c->plan.grid_dim;
   out->graph_replayed = c->last_replayed ? 1 : 0;
+  out->tune_cache_hit = c->tune_cache_hit;
   return FSBM_OK;
 }
 
@@ -940,6 +1044,7 @@ int32_t* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 extern "C" fsbm_status fsbm_coal_step_noalloc(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points,
                                               double dt, int32_t n_steps) {
+  NvtxRange nvtx_("fsbm_coal_step_noalloc");
   if (!c) return FSBM_E_ARG;
   fsbm_status st = check_state(c, s, n_points, dt, n_steps, "fsbm_coal_step_noalloc");
   if (st != FSBM_OK) return st;

@@ -36,6 +36,7 @@ constexpr float kLnBottEps = -138.15510557964274f;
 
 struct GridDev {
   int n;
+  unsigned inv_n;                 // floor(2^32 / n) + 1: e / n = umulhi(e, inv_n) for e < 5 n
   int kappa_max;                  // kappa[0]
   int d_lo[kMaxKappa + 1];        // D_kappa = {d : kappa[d] = kappa} = [d_lo, d_hi]
   int d_hi[kMaxKappa + 1];
