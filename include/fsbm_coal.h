@@ -318,6 +318,15 @@ FSBM_API fsbm_status fsbm_coal_get_active_list(fsbm_coal_ctx* ctx, int32_t* out,
  * and the reciprocal square root and reciprocal (relative). Synchronous; allocates 40 bytes. */
 FSBM_API fsbm_status fsbm_coal_math_check(fsbm_coal_ctx* ctx, double* out5);
 
+/* The bounds-checked build of this library (libfsbm_coal_checked.so, the same entry points
+ * compiled with -DFSBM_CHECKED) checks, before every kernel walks a range of indices, the
+ * range's ends against its arrays, skips a range that fails and counts the failure instead of
+ * trapping. out4[0] receives the failures counted since the previous call (then reset), out4[1]
+ * the source line of the first one, out4[2] and out4[3] its index and bound (low 32 bits).
+ * Synchronises the context's stream. The normal build returns FSBM_E_UNSUPPORTED with zeros.
+ * The paper has no counterpart; it stands in for a memory checker on small cases. */
+FSBM_API fsbm_status fsbm_coal_check_record(fsbm_coal_ctx* ctx, uint32_t* out4);
+
 /* Free the context and everything it owns. NULL is accepted. */
 FSBM_API fsbm_status fsbm_coal_destroy(fsbm_coal_ctx* ctx);
 

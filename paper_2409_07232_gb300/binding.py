@@ -18,6 +18,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfsbm_coal.so")
+# FSBM_LIBRARY=checked selects the bounds-checked build (same entry points, fsbm_coal_check_record)
+LIB_CHECKED_PATH = os.path.join(HERE, "libfsbm_coal_checked.so")
 
 FSBM_OK = 0
 FSBM_E_ARG = -1
@@ -40,7 +42,8 @@ _STATUS_NAMES = {0: "FSBM_OK", -1: "FSBM_E_ARG", -2: "FSBM_E_CUDA", -3: "FSBM_E_
 EXPORTS = ("fsbm_coal_init", "fsbm_coal_clone", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_step_noalloc", "fsbm_coal_step_wrf",
            "fsbm_coal_step_shard", "fsbm_coal_shard_bounds", "fsbm_coal_autotune", "fsbm_coal_autotune_steps",
            "fsbm_coal_set_graph", "fsbm_coal_set_block", "fsbm_coal_set_timing", "fsbm_coal_get_stats",
-           "fsbm_coal_get_active_list", "fsbm_coal_math_check", "fsbm_coal_destroy", "fsbm_coal_last_error")
+           "fsbm_coal_get_active_list", "fsbm_coal_math_check", "fsbm_coal_check_record", "fsbm_coal_destroy",
+           "fsbm_coal_last_error")
 
 
 class FsbmError(RuntimeError):
@@ -121,12 +124,15 @@ _lock = threading.Lock()
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libfsbm_coal.so and declare every entry point's signature."""
+def load(path: str = None):
+    """Load libfsbm_coal.so (or, with FSBM_LIBRARY=checked in the environment, its bounds-checked
+    build) and declare every entry point's signature."""
     global _lib
     with _lock:
-        if _lib is not None:
+        if _lib is not None and path is None:
             return _lib
+        if path is None:
+            path = LIB_CHECKED_PATH if os.environ.get("FSBM_LIBRARY") == "checked" else LIB_PATH
         if not os.path.exists(path):
             raise ImportError(f"{path} is missing: build it with "
                               "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
@@ -153,6 +159,7 @@ def load(path: str = LIB_PATH):
             "fsbm_coal_get_stats": ([V, P(fsbm_coal_stats)], ctypes.c_int),
             "fsbm_coal_get_active_list": ([V, V, ctypes.c_int64, P(ctypes.c_int64)], ctypes.c_int),
             "fsbm_coal_math_check": ([V, V], ctypes.c_int),
+            "fsbm_coal_check_record": ([V, V], ctypes.c_int),
             "fsbm_coal_destroy": ([V], ctypes.c_int),
             "fsbm_coal_last_error": ([V], ctypes.c_char_p),
         }
@@ -309,6 +316,14 @@ def fsbm_coal_get_active_list(ctx, cap: int) -> np.ndarray:
 def fsbm_coal_math_check(ctx) -> np.ndarray:
     out = np.zeros(5, np.float64)
     _check(ctx, load().fsbm_coal_math_check(ctx, out.ctypes.data), "fsbm_coal_math_check")
+    return out
+
+
+def fsbm_coal_check_record(ctx) -> np.ndarray:
+    """Failures counted by the bounds-checked build since the last call, the first one's source
+    line, index and bound (FsbmError FSBM_E_UNSUPPORTED from the normal build)."""
+    out = np.zeros(4, np.uint32)
+    _check(ctx, load().fsbm_coal_check_record(ctx, out.ctypes.data), "fsbm_coal_check_record")
     return out
 
 

@@ -1,8 +1,9 @@
 """Compile the CUDA library (libfsbm_coal.so) in-tree with nvcc for sm_103a.
 
 The translation units compile in parallel into ``_build/`` and link into
-``paper_2409_07232_gb300/libfsbm_coal.so``. A rebuild happens only when a source or the
-public header is newer than the library.
+``paper_2409_07232_gb300/libfsbm_coal.so``; the same sources with ``-DFSBM_CHECKED`` give the
+bounds-checked ``libfsbm_coal_checked.so`` (``_build/checked/``). A rebuild happens only when a
+source or the public header is newer than the library.
 """
 from __future__ import annotations
 
@@ -15,6 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsbm_coal.so")
+LIB_CHECKED = os.path.join(HERE, "libfsbm_coal_checked.so")
 HEADER = os.path.join(ROOT, "include", "fsbm_coal.h")
 SOURCES = ["compact.cu", "coal_kernel.cu", "sweep_kernel.cu", "wrf_frontend.cu", "fsbm_coal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,31 +39,42 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def _build_variant(lib: str, build_dir: str, defines, force: bool, verbose: bool):
+    os.makedirs(build_dir, exist_ok=True)
     headers = [HEADER] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    objs = []
-    jobs = []
+    objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([_nvcc(), *ARCH, *FLAGS, *EXTRA.get(src, []), "-c", s, "-o", o])
+            jobs.append([_nvcc(), *ARCH, *FLAGS, *defines, *EXTRA.get(src, []), "-c", s, "-o", o])
+    link = None
+    if force or jobs or _stale(lib, objs):
+        link = [_nvcc(), *ARCH, "-shared", "-o", lib + f".tmp{os.getpid()}", *objs, "-lcudart"]
+    return jobs, link
 
-    def run(cmd):
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
-        if verbose:
-            print(r.stdout + r.stderr)
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, LIB)
+def _run(cmd, verbose=False):
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+    if verbose:
+        print(r.stdout + r.stderr)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Build libfsbm_coal.so and its bounds-checked twin libfsbm_coal_checked.so (the same
+    sources with -DFSBM_CHECKED); returns the path of the first."""
+    variants = [(LIB, BUILD, []), (LIB_CHECKED, os.path.join(BUILD, "checked"), ["-DFSBM_CHECKED"])]
+    plans = [_build_variant(lib, bdir, defs, force, verbose) for lib, bdir, defs in variants]
+    jobs = [j for p in plans for j in p[0]]
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
+        list(ex.map(lambda c: _run(c, verbose), jobs))
+    for (lib, _, _), (_, link) in zip(variants, plans):
+        if link:
+            _run(link, verbose)
+            os.replace(link[link.index("-o") + 1], lib)
     return LIB
 
 

@@ -401,6 +401,7 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
   const T* __restrict__ cds = sm.cd;
   const int lo_s = lo[o.s], hi_s = hi[o.s], lo_l = lo[o.l], hi_l = hi[o.l];
   on = on && k >= 1 && k < n;
+  if (FSBM_CHECKED_BUILD && on && !TOP && !FSBM_OK(G.chk, k + 1, n)) on = false;
   TargetOf<T> tgt;
   if (!TOP) tgt.init(on ? sm.Mt[o.c * n + k] : T(0), on ? sm.Mt[o.c * n + k + 1] : T(0), B, mt);
   const int kstride = n * S2;
@@ -410,6 +411,10 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
     const int m1 = on ? min(TOP ? n - 1 : k - kap, hi_l) : m0 - 1;
     for (int m = m0; m <= m1; ++m) {
       const int d0 = max(dlo, m - hi_s), d1 = min(dhi, m - lo_s);
+      if (FSBM_CHECKED_BUILD && d0 <= d1 &&
+          !(FSBM_OK(G.chk, d0, n) && FSBM_OK(G.chk, d1, n) && FSBM_OK(G.chk, m, n) && FSBM_OK(G.chk, m - d1, n) &&
+            FSBM_OK(G.chk, m - d0, n) && FSBM_OK(G.chk, ((ptrdiff_t)d1 * n + m) * S2 + o.table, (ptrdiff_t)S2 * n * n)))
+        continue;
       const T am = Ml[m] * dt;
       const T ll = LIMITED ? Ll[m] : T(1);
       const ptrdiff_t e0 = (ptrdiff_t)(d0 * n + m) * S2;
@@ -418,7 +423,28 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
       // runs of up to kGainRun pairs, each folded into the running totals after it
       for (int dc = d0; dc <= d1; dc += kGainRun) {
         const int dce = min(d1, dc + kGainRun - 1);
-        for (int d = dc; d <= dce; ++d, Kp += kstride) {
+        int d = dc;
+        if (sizeof(T) == sizeof(float) && !LEVELS) {
+          // FP32: two pairs per iteration, so that two flux chains (each a string of dependent
+          // SFU and FMA operations) are in flight per lane; the sums take them in pair order
+          for (; d + 1 <= dce; d += 2, Kp += 2 * kstride) {
+            const int i = m - d;
+            const T K0 = __ldg(Kp), K1 = __ldg(Kp + kstride);
+            T dM0 = K0 * am * Ns[i], dM1 = K1 * am * Ns[i - 1];
+            if (LIMITED) {
+              dM0 *= min_nonneg(Ls[i], ll);
+              dM1 *= min_nonneg(Ls[i - 1], ll);
+            }
+            stay.add(dM0);
+            stay.add(dM1);
+            if (!TOP) {
+              const T f0 = tgt.flux(dM0, cds[d], mt), f1 = tgt.flux(dM1, cds[d + 1], mt);
+              up.add(f0);
+              up.add(f1);
+            }
+          }
+        }
+        for (; d <= dce; ++d, Kp += kstride) {
           const int i = m - d;
           T K = __ldg(Kp);
           if (LEVELS) {
@@ -480,12 +506,18 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
     const int idx = s_next;
     __syncthreads();
     if (idx >= n_end) break;
+    if (FSBM_CHECKED_BUILD && !FSBM_OK(t.chk, idx, counters[0])) break;
     const int p = list[idx];
+    if (FSBM_CHECKED_BUILD && !FSBM_OK(t.chk, p, pd.n_points)) continue;
     const int g = pd.grid_id[p];
+    if (FSBM_CHECKED_BUILD && !FSBM_OK(t.chk, g, t.G)) continue;
     const GridDev& G = t.g[g];
     const int n = G.n;
     const unsigned mask = pd.species_mask[p];
     const int ns = __popc(mask);
+    if (FSBM_CHECKED_BUILD && !(FSBM_OK(t.chk, n - 1, nmax) && FSBM_OK(t.chk, ns - 1, S) &&
+                                FSBM_OK(t.chk, pd.offset[p + 1] - pd.offset[p] - (int64_t)ns * n, 1)))
+      continue;
     const int64_t off = pd.offset[p];
     Store* spec = reinterpret_cast<Store*>(pd.spectra) + off;
     const int E = ns * n;
@@ -594,9 +626,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       __syncthreads();
 
       // 2. requested loss R and limiter ratios (one lane per row (a, i); Kr is i-fastest, so
-      //    a warp's loads of one column are contiguous). Each lane keeps four partial sums
-      //    (columns j, j+1, j+2, j+3) so that four loads are in flight at once; the partials
-      //    are added in a fixed order.
+      //    a warp's loads of one column are contiguous). Each lane keeps eight partial sums
+      //    (columns j .. j+7) so that eight loads are in flight at once; the partials are
+      //    added in a fixed order.
       const T* __restrict__ Kr = Sel<T>::Kr(G);
       const T* __restrict__ Krd = lev ? Sel<T>::Kr_d(G) : nullptr;
       bool fired = false;
@@ -608,33 +640,35 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           Acc<T> acc;
           for (int b = 0; b < ns; ++b) {
             const size_t base = (size_t)(s_sp[a] * S + s_sp[b]) * n * n + i;
+            if (FSBM_CHECKED_BUILD && s_lo[b] <= s_hi[b] &&
+                !(FSBM_OK(t.chk, s_lo[b], n) && FSBM_OK(t.chk, base + (size_t)s_hi[b] * n, (size_t)S * S * n * n)))
+              continue;
             const T* __restrict__ Kab = Kr + base;
             const T* __restrict__ Kabd = lev ? Krd + base : nullptr;
             const T* __restrict__ Nb = sm.N + b * n;
             for (int j0 = s_lo[b]; j0 <= s_hi[b]; j0 += kLossRun) {
               const int j1 = min(s_hi[b], j0 + kLossRun - 1);
-              T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+              T p[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) p[u] = T(0);
               int j = j0;
-              for (; j + 3 <= j1; j += 4) {
-                T k0 = __ldg(Kab + (size_t)j * n), k1 = __ldg(Kab + (size_t)(j + 1) * n);
-                T k2 = __ldg(Kab + (size_t)(j + 2) * n), k3 = __ldg(Kab + (size_t)(j + 3) * n);
+              for (; j + 7 <= j1; j += 8) {
+                T kk[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) kk[u] = __ldg(Kab + (size_t)(j + u) * n);
                 if (lev) {
-                  k0 = fma(wT, __ldg(Kabd + (size_t)j * n), k0);
-                  k1 = fma(wT, __ldg(Kabd + (size_t)(j + 1) * n), k1);
-                  k2 = fma(wT, __ldg(Kabd + (size_t)(j + 2) * n), k2);
-                  k3 = fma(wT, __ldg(Kabd + (size_t)(j + 3) * n), k3);
+#pragma unroll
+                  for (int u = 0; u < 8; ++u) kk[u] = fma(wT, __ldg(Kabd + (size_t)(j + u) * n), kk[u]);
                 }
-                p0 = fma(k0, Nb[j], p0);
-                p1 = fma(k1, Nb[j + 1], p1);
-                p2 = fma(k2, Nb[j + 2], p2);
-                p3 = fma(k3, Nb[j + 3], p3);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) p[u] = fma(kk[u], Nb[j + u], p[u]);
               }
               for (; j <= j1; ++j) {
                 T k0 = __ldg(Kab + (size_t)j * n);
                 if (lev) k0 = fma(wT, __ldg(Kabd + (size_t)j * n), k0);
-                p0 = fma(k0, Nb[j], p0);
+                p[0] = fma(k0, Nb[j], p[0]);
               }
-              acc.add((p0 + p1) + (p2 + p3));
+              acc.add(((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
               acc.flush();
             }
           }
@@ -655,7 +689,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       //      = lam_i R_i + dt M_i sum_{j limited} K N_j (min(lam_i, lam_j) - lam_i),
       //    where lam_i R_i = M_i when lam_i < 1 and every term with lam_j >= lam_i is 0. The
       //    sum runs over the rows whose ratio fired, gathered once in row order; each row
-      //    walks that list with four partial sums, added in a fixed order.
+      //    walks that list with eight partial sums, added in a fixed order.
       if (limited) {
         if (warp == 0) {
           int cnt = 0;
@@ -663,7 +697,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
             const int r = r0 + lane;
             const bool f = r < E && sm.lam[r] < T(1);
             const unsigned bal = __ballot_sync(0xffffffffu, f);
-            if (f) sm.lim[cnt + __popc(bal & ((1u << lane) - 1u))] = r;
+            if (f && FSBM_OK(t.chk, cnt + __popc(bal & ((1u << lane) - 1u)), E))
+              sm.lim[cnt + __popc(bal & ((1u << lane) - 1u))] = r;
             cnt += __popc(bal);
           }
           if (lane == 0) s_nlim = cnt;
@@ -676,39 +711,41 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           sm.llam[q] = sm.lam[r];
           sm.lN[q] = sm.N[r];
           sm.loff[q] = (s_sp[b] * n + j) * n;
+          if (FSBM_CHECKED_BUILD && !FSBM_OK(t.chk, (size_t)(S - 1) * S * n * n + (n - 1) + sm.loff[q], (size_t)S * S * n * n))
+            sm.loff[q] = 0;
         }
         __syncthreads();
         for (int r = tid; r < E; r += NT) {
           const int a = div_n(r, G.inv_n), i = r - a * n;
           if (i < s_lo[a] || i > s_hi[a]) continue;
           const T li = sm.lam[r];
+          if (FSBM_CHECKED_BUILD && !(FSBM_OK(t.chk, s_sp[a], S) && FSBM_OK(t.chk, L, E + 1))) continue;
           const T* __restrict__ Kri = Kr + (size_t)s_sp[a] * S * n * n + i;
           const T* __restrict__ Krid = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
           Acc<T> acc;
           for (int q0 = 0; q0 < L; q0 += kLossRun) {
             const int q1 = min(L, q0 + kLossRun);
-            T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+            T p[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) p[u] = T(0);
             int q = q0;
-            for (; q + 3 < q1; q += 4) {
-              T k0 = __ldg(Kri + sm.loff[q]), k1 = __ldg(Kri + sm.loff[q + 1]);
-              T k2 = __ldg(Kri + sm.loff[q + 2]), k3 = __ldg(Kri + sm.loff[q + 3]);
+            for (; q + 7 < q1; q += 8) {
+              T kk[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) kk[u] = __ldg(Kri + sm.loff[q + u]);
               if (lev) {
-                k0 = fma(wT, __ldg(Krid + sm.loff[q]), k0);
-                k1 = fma(wT, __ldg(Krid + sm.loff[q + 1]), k1);
-                k2 = fma(wT, __ldg(Krid + sm.loff[q + 2]), k2);
-                k3 = fma(wT, __ldg(Krid + sm.loff[q + 3]), k3);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) kk[u] = fma(wT, __ldg(Krid + sm.loff[q + u]), kk[u]);
               }
-              p0 = fma((min_nonneg(li, sm.llam[q]) - li) * k0, sm.lN[q], p0);
-              p1 = fma((min_nonneg(li, sm.llam[q + 1]) - li) * k1, sm.lN[q + 1], p1);
-              p2 = fma((min_nonneg(li, sm.llam[q + 2]) - li) * k2, sm.lN[q + 2], p2);
-              p3 = fma((min_nonneg(li, sm.llam[q + 3]) - li) * k3, sm.lN[q + 3], p3);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) p[u] = fma((min_nonneg(li, sm.llam[q + u]) - li) * kk[u], sm.lN[q + u], p[u]);
             }
             for (; q < q1; ++q) {
               T k0 = __ldg(Kri + sm.loff[q]);
               if (lev) k0 = fma(wT, __ldg(Krid + sm.loff[q]), k0);
-              p0 = fma((min_nonneg(li, sm.llam[q]) - li) * k0, sm.lN[q], p0);
+              p[0] = fma((min_nonneg(li, sm.llam[q]) - li) * k0, sm.lN[q], p[0]);
             }
-            acc.add((p0 + p1) + (p2 + p3));
+            acc.add(((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
             acc.flush();
           }
           const double base = li < T(1) ? sm.M[r] : sm.loss[r];
@@ -767,7 +804,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
             }
           }
 #undef FSBM_GAIN
-          if (on) {
+          if (on && FSBM_OK(t.chk, ol * n + k, O * n)) {
             sm.stay[ol * n + k] = st_;
             sm.up[ol * n + k] = up_;
           }
@@ -786,6 +823,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
         typename Num<T>::Sum gsum = Num<T>::zero();
         for (int qq = 0; qq < s_np[c]; ++qq) {
           const int q = s_plist[c][qq];
+          if (FSBM_CHECKED_BUILD && !FSBM_OK(t.chk, (size_t)q * n + k, (size_t)O * n)) continue;
           Num<T>::add(gsum, sm.stay[q * n + k]);
           if (k > 0) Num<T>::add(gsum, sm.up[q * n + k - 1]);
         }

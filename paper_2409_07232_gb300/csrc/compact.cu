@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_classify(Tables t, PointsDe
     if (lane == 0) wc[b][warp] = __popc(m);
   }
   __syncthreads();
-  if (threadIdx.x < nb) {
+  if (threadIdx.x < nb && FSBM_OK(t.chk, (int64_t)threadIdx.x * n_blocks + blockIdx.x, (int64_t)kNumBuckets * n_blocks)) {
     int s = 0;
     for (int w = 0; w < kWarps; ++w) s += wc[threadIdx.x][w];
     block_counts[(int64_t)threadIdx.x * n_blocks + blockIdx.x] = s;
@@ -158,7 +158,8 @@ __global__ void __launch_bounds__(kCompactThreads) k_scatter(Tables t, PointsDev
     const unsigned same = __match_any_sync(__activemask(), r);
     int rank = __popc(same & ((1u << lane) - 1u));
     for (int w = 0; w < warp; ++w) rank += wc[r][w];
-    list[offsets[(int64_t)r * n_blocks + blockIdx.x] + rank] = (int32_t)p;
+    if (FSBM_OK(t.chk, offsets[(int64_t)r * n_blocks + blockIdx.x] + rank, n_points))
+      list[offsets[(int64_t)r * n_blocks + blockIdx.x] + rank] = (int32_t)p;
   }
 }
 

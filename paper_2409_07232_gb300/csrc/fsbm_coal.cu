@@ -189,8 +189,9 @@ fsbm_status check_state(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
   return FSBM_OK;
 }
 
-PointsDev to_dev(const fsbm_coal_state* s) {
+PointsDev to_dev(const fsbm_coal_state* s, int64_t n_points) {
   PointsDev p;
+  p.n_points = n_points;
   p.spectra = s->spectra;
   p.offset = s->offset;
   p.grid_id = s->grid_id;
@@ -348,6 +349,14 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
   c->G = G;
   c->precision = cfg->precision;
   c->stream = static_cast<cudaStream_t>(stream);
+#ifdef FSBM_CHECKED
+  {
+    const unsigned* chk = nullptr;
+    const std::vector<unsigned> zero(4, 0u);
+    if (upload(c, zero, &chk) != FSBM_OK) return bail(FSBM_E_CUDA);
+    c->t.chk = const_cast<unsigned*>(chk);
+  }
+#endif
   c->t.S = S;
   c->t.mode = cfg->mode;
   c->t.G = G;
@@ -386,6 +395,7 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
       cls.push_back(Cls{(double)ns * n * (n + 1) / 2.0 + (double)ns * (ns - 1) / 2.0 * (double)n * n, g, ns});
 
     GridDev& gd = c->t.g[g];
+    gd.chk = c->t.chk;
     gd.n = n;
     gd.inv_n = (unsigned)((uint64_t(1) << 32) / (uint64_t)n + 1);
     std::vector<int> kap;
@@ -546,7 +556,7 @@ fsbm_status fsbm_coal_step(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n
   if (!c) return FSBM_E_ARG;
   fsbm_status st = check_state(c, s, n_points, dt, n_steps);
   if (st != FSBM_OK) return st;
-  return run_step(c, to_dev(s), n_points, dt, n_steps);
+  return run_step(c, to_dev(s, n_points), n_points, dt, n_steps);
 }
 
 fsbm_status fsbm_coal_step_shard(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_points, double dt,
@@ -557,7 +567,7 @@ fsbm_status fsbm_coal_step_shard(fsbm_coal_ctx* c, const fsbm_coal_state* s, int
   if (st != FSBM_OK) return st;
   if (n_shards < 1 || n_shards > kMaxShards || shard < 0 || shard >= n_shards)
     return fail(c, FSBM_E_ARG, "fsbm_coal_step_shard: need 0 <= shard < n_shards <= 1024");
-  return run_step(c, to_dev(s), n_points, dt, n_steps, shard, n_shards);
+  return run_step(c, to_dev(s, n_points), n_points, dt, n_steps, shard, n_shards);
 }
 
 fsbm_status fsbm_coal_shard_bounds(const int64_t* run_count, const int64_t* run_cost, int32_t n_runs,
@@ -632,6 +642,7 @@ fsbm_status fsbm_coal_step_host(fsbm_coal_ctx* c, const fsbm_coal_state* h, int6
   const bool has_p = h->pressure && c->t.levels;
   if (has_p) CU(c, cudaMemcpyAsync(d_P, h->pressure, sizeof(float) * n, cudaMemcpyHostToDevice, sm));
   PointsDev p;
+  p.n_points = n_points;
   p.spectra = d_spec - (size_t)base * esz;  // the offsets index from the caller's base
   p.offset = d_off;
   p.grid_id = d_gid;
@@ -667,6 +678,7 @@ fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* c, const fsbm_wrf_state* w, double
   if (w->its < w->ims || w->ite > w->ime || w->kts < w->kms || w->kte > w->kme || w->jts < w->jms || w->jte > w->jme)
     return fail(c, FSBM_E_ARG, "fsbm_coal_step_wrf: tile ranges outside the memory ranges");
   WrfDev d{};
+  d.chk = c->t.chk;
   d.ns = 0;
   d.mask = 0;
   for (int a = 0; a < c->S; ++a)
@@ -728,6 +740,7 @@ fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* c, const fsbm_wrf_state* w, double
   }
   char* m = static_cast<char*>(c->wrf_meta);
   PointsDev p{};
+  p.n_points = n_tile;
   p.offset = reinterpret_cast<int64_t*>(m);
   m += sizeof(int64_t) * (n + 1);
   p.mass_budget = reinterpret_cast<double*>(m);
@@ -801,7 +814,7 @@ fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
   const size_t outb = (sizeof(double) * 2 + sizeof(int32_t)) * (size_t)P;
   CU(c, cudaMalloc(&tmp, bytes + outb + 64));
   char* src = static_cast<char*>(s->spectra) + (size_t)off[0] * esz;
-  PointsDev p = to_dev(s);
+  PointsDev p = to_dev(s, P);
   p.spectra = tmp - (size_t)off[0] * esz;
   p.mass_budget = reinterpret_cast<double*>(tmp + ((bytes + 15) & ~size_t(15)));
   p.mass_error = p.mass_budget + P;
@@ -1008,6 +1021,20 @@ fsbm_status fsbm_coal_math_check(fsbm_coal_ctx* c, double* out5) {
   return FSBM_OK;
 }
 
+fsbm_status fsbm_coal_check_record(fsbm_coal_ctx* c, uint32_t* out4) {
+  if (!c || !out4) return FSBM_E_ARG;
+#ifdef FSBM_CHECKED
+  CU(c, cudaStreamSynchronize(c->stream));
+  CU(c, cudaMemcpy(out4, c->t.chk, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  CU(c, cudaMemset(c->t.chk, 0, 4 * sizeof(uint32_t)));
+  return FSBM_OK;
+#else
+  out4[0] = out4[1] = out4[2] = out4[3] = 0;
+  return fail(c, FSBM_E_UNSUPPORTED, "fsbm_coal_check_record: this library is built without bounds checks "
+                                     "(libfsbm_coal_checked.so has them)");
+#endif
+}
+
 const char* fsbm_coal_last_error(const fsbm_coal_ctx* c) { return c ? c->err.c_str() : kNullCtxMsg; }
 
 }  // extern "C"
@@ -1075,7 +1102,7 @@ extern "C" fsbm_status fsbm_coal_step_noalloc(fsbm_coal_ctx* c, const fsbm_coal_
   sc.block_counts = base;
   sc.active_list = base + (int64_t)kNumBuckets * kNoAllocMaxBlocks;
   sc.counters = sc.active_list + kNoAllocMaxPoints;
-  const PointsDev p = to_dev(s);
+  const PointsDev p = to_dev(s, n_points);
   CU(c, launch_compact(c->t, p, n_points, sc, c->stream));
   CU(c, launch_coal(c->t, c->precision, p, sc, dt, n_steps, c->plan, c->stream));
   return FSBM_OK;

@@ -22,6 +22,32 @@
 
 namespace fsbm {
 
+// Bounds-checked build (compiled with -DFSBM_CHECKED into libfsbm_coal_checked.so): before a
+// kernel walks a range of indices it checks the range's ends (a point's list slot, grid, bin
+// count and element count; a gain group's bins, distances and table entries; a loss row's
+// columns; a compaction slot; a WRF-layout element) against the arrays' sizes. A failed check
+// adds one to the context's check record, keeps the first failing source line, index and bound,
+// and the kernel skips that range: nothing traps and no access leaves its array. The normal
+// build compiles the checks out.
+#ifdef FSBM_CHECKED
+__device__ __forceinline__ bool fsbm_in_range(unsigned* chk, long long i, long long bound, int line) {
+  if (i >= 0 && i < bound) return true;
+  if (chk) {
+    atomicAdd(chk, 1u);
+    if (atomicCAS(chk + 1, 0u, (unsigned)line) == 0u) {
+      chk[2] = (unsigned)i;
+      chk[3] = (unsigned)bound;
+    }
+  }
+  return false;
+}
+#define FSBM_OK(chk, i, bound) fsbm_in_range((chk), (long long)(i), (long long)(bound), __LINE__)
+#define FSBM_CHECKED_BUILD 1
+#else
+#define FSBM_OK(chk, i, bound) true
+#define FSBM_CHECKED_BUILD 0
+#endif
+
 constexpr int kMaxSpecies = 5;
 constexpr int kMaxGrids = 4;
 constexpr int kMaxBins = 512;
@@ -35,6 +61,7 @@ constexpr double kBottEps = 1e-60;
 constexpr float kLnBottEps = -138.15510557964274f;
 
 struct GridDev {
+  unsigned* chk;                  // check record of the bounds-checked build (else NULL)
   int n;
   unsigned inv_n;                 // floor(2^32 / n) + 1: e / n = umulhi(e, inv_n) for e < 5 n
   int kappa_max;                  // kappa[0]
@@ -60,6 +87,7 @@ struct GridDev {
 };
 
 struct Tables {
+  unsigned* chk;                  // check record of the bounds-checked build (else NULL)
   int S;
   int G;
   int64_t rank_cost[kMaxGrids * kMaxSpecies];  // bin pairs per step of a point of each LPT rank
@@ -76,6 +104,7 @@ struct Tables {
 
 // Caller-owned per-point arrays (device pointers).
 struct PointsDev {
+  int64_t n_points;
   void* spectra;
   const int64_t* offset;
   const uint8_t* grid_id;
@@ -155,6 +184,7 @@ cudaError_t launch_coal(const Tables& t, int precision, const PointsDev& p, cons
 // WRF-layout fields (the public fsbm_wrf_state, resolved): memory extents, tile extents and the
 // carried species in slot order.
 struct WrfDev {
+  unsigned* chk;                // check record of the bounds-checked build (else NULL)
   const void* ff[kMaxSpecies];  // by slot (species id sp[s])
   int ns;
   int n;                        // bins of the grid

@@ -54,7 +54,9 @@ __global__ void k_sweep(Tables t, PointsDev pd, const int32_t* __restrict__ list
   const int q0 = counters[1], q1 = counters[2];  // the list part this call steps
   const int S = t.S;
   for (int q = q0 + blockIdx.x * blockDim.x + threadIdx.x; q < q1; q += gridDim.x * blockDim.x) {
+    if (FSBM_CHECKED_BUILD && !FSBM_OK(t.chk, q, counters[0])) break;
     const int p = list[q];
+    if (FSBM_CHECKED_BUILD && !(FSBM_OK(t.chk, p, pd.n_points) && FSBM_OK(t.chk, pd.grid_id[p], t.G))) continue;
     const GridDev& G = t.g[pd.grid_id[p]];
     const int n = G.n;
     const unsigned mask = pd.species_mask[p];
@@ -62,6 +64,7 @@ __global__ void k_sweep(Tables t, PointsDev pd, const int32_t* __restrict__ list
     int ns = 0;
     for (int a = 0; a < S; ++a)
       if (mask >> a & 1u) sp[ns++] = a;
+    if (FSBM_CHECKED_BUILD && !FSBM_OK(t.chk, pd.offset[p + 1] - pd.offset[p] - (int64_t)ns * n, 1)) continue;
     double* M = reinterpret_cast<double*>(pd.spectra) + pd.offset[p];
     const int E = ns * n;
     bool bad = false;
@@ -130,6 +133,8 @@ __global__ void k_sweep(Tables t, PointsDev pd, const int32_t* __restrict__ list
               const double xj = x[j];
               const double Ni = Ma[i] / xi, Nj = Mb[j] / xj;
               const int dd = i < j ? j - i : i - j;
+              if (FSBM_CHECKED_BUILD && !(FSBM_OK(t.chk, i, n) && FSBM_OK(t.chk, j, n) && FSBM_OK(t.chk, cs, ns)))
+                continue;
               const int k = (i > j ? i : j) + kapd[dd];
               double K = __ldg(Kab + (size_t)j * n + i);
               if (Krd) K = K + wlev * __ldg(Krd + (size_t)(sp[sa] * S + sp[sb]) * n * n + (size_t)j * n + i);

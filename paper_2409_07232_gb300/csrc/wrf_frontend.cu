@@ -29,6 +29,7 @@ __global__ void k_wrf_meta(WrfDev w, PointsDev pk, int64_t n_tile) {
   if (q == 0) const_cast<int64_t*>(pk.offset)[n_tile] = n_tile * slot;
   if (q >= n_tile) return;
   const int64_t m = mem_index(w, q);
+  if (FSBM_CHECKED_BUILD && !FSBM_OK(w.chk, m, (int64_t)w.im * w.km * w.jm)) return;
   const_cast<int64_t*>(pk.offset)[q] = q * slot;
   const_cast<uint8_t*>(pk.grid_id)[q] = (uint8_t)w.grid;
   const_cast<uint8_t*>(pk.species_mask)[q] = (uint8_t)w.mask;
@@ -46,6 +47,7 @@ __global__ void k_wrf_pack(WrfDev w, PointsDev pk, int64_t n_tile, double t_min)
   const int e = blockIdx.y, s = e / w.n, b = e - s * w.n;
   const int64_t plane = (int64_t)w.im * w.km * w.jm;
   const T* src = static_cast<const T*>(w.ff[s]);
+  if (FSBM_CHECKED_BUILD && !(FSBM_OK(w.chk, mem_index(w, q), plane) && FSBM_OK(w.chk, s, w.ns))) return;
   static_cast<T*>(pk.spectra)[q * ((int64_t)w.ns * w.n) + e] = src[(int64_t)b * plane + mem_index(w, q)];
 }
 
@@ -57,6 +59,7 @@ __global__ void k_wrf_unpack(WrfDev w, PointsDev pk, int64_t n_tile) {
   const int st = pk.status[q];
   const int64_t m = mem_index(w, q);
   const int e = blockIdx.y;
+  if (FSBM_CHECKED_BUILD && !FSBM_OK(w.chk, m, (int64_t)w.im * w.km * w.jm)) return;
   if (e == 0) {
     if (w.status) w.status[m] = st;
     if (w.mass_budget) w.mass_budget[m] = pk.mass_budget[q];
