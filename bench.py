@@ -53,20 +53,25 @@ import numpy as np  # noqa: E402
 SMS = 152
 FP32_LANES = 128            # FP32 FMA-pipe operations per clock per SM
 MUFU_LANES = 16             # special-function (lg2/ex2/rcp/rsq) results per clock per SM
-FP64_PER_CLK = 2            # FP64 operations per clock per SM (the probe measured 1.64-1.73)
+FP64_PER_CLK = 2            # FP64 operations per clock per SM (GB300 nominal, 1.25 TFLOP/s)
 # Algorithmic operations of one bin-pair interaction (one unordered pair, one step) as the
-# method is formulated here (per-target constants hoisted; table-driven FP64 transcendentals
-# after Tang; SFU-seeded reciprocal and square root), counted from the formula, plus the
-# requested-loss mat-vec (2 multiply-adds per unordered pair):
-#  FP32 form: dM 3, sums 2, g 1, rho 1, ln 3, clamp 2, sqrt 1, z 1, test 1,
-#             (1 - e^-z)/z series 12, F and clip 3, mat-vec 2 = 32 FMA-pipe operations,
-#             and 4 SFU operations (reciprocal, log2, reciprocal square root, and one more
-#             in the exponential branch);
-#  FP64 form: dM 3, sums 2, g 1, ln 10, x1 1, e^{x1/2} 6, z 1, e^y - 1 11, F 6,
-#             mat-vec 2 = 43 FP64-pipe operations.
-FP_OPS_PER_PAIR = 32
-MUFU_OPS_PER_PAIR = 4
-FP64_OPS_PER_PAIR = 43
+# method is formulated in the kernels (per-target constants hoisted; kernel table entries
+# pre-scaled by (x_i + x_m) / x_m; table-driven FP64 transcendentals after Tang; SFU-seeded
+# reciprocal and square root), counted from the formula, plus the requested-loss mat-vec
+# (2 multiply-adds per unordered pair):
+#  FP32 form (one branch-free flux, both of its forms evaluated): dM 2, sums 2, g 1, rho 1,
+#             x1 1, clamp 2, z 1, exponent arguments 2, z^2 1, sinh series 3, near-zero form
+#             2, far form 2, select 2, F and clip 3, mat-vec 2 = 27 FMA-pipe operations, and 5
+#             SFU operations (two reciprocals, log2, two exponentials);
+#  FP64 form: dM 2, sums 2, g 1, ln 9, x1 1, e^{x1/2} 6, z 1, e^y - 1 11, F 6,
+#             mat-vec 2 = 41 FP64-pipe operations.
+FP_OPS_PER_PAIR = 27
+MUFU_OPS_PER_PAIR = 5
+FP64_OPS_PER_PAIR = 41
+# SWEEP (Bott's in-place order, one thread per point, CUDA's log/exp/expm1 and IEEE
+# divisions): FP64 DADD + DMUL + DFMA thread instructions per bin pair and step, counted by
+# ncu on k_sweep (profiles/k_sweep_conus20k_fp64_ops.md)
+SWEEP_FP64_OPS_PER_PAIR = 114.3
 
 
 L2_BYTES = 129e6
@@ -116,10 +121,10 @@ def pairs_per_point(n, ns):
     return ns * n * (n + 1) // 2 + ns * (ns - 1) // 2 * n * n
 
 
-def alu_peak_pairs(precision, sm_mhz):
+def alu_peak_pairs(precision, sm_mhz, fp64_ops=None):
     f = sm_mhz * 1e6
     if precision == 0:
-        return SMS * FP64_PER_CLK * f / FP64_OPS_PER_PAIR
+        return SMS * FP64_PER_CLK * f / (fp64_ops or FP64_OPS_PER_PAIR)
     return min(SMS * FP32_LANES * f / FP_OPS_PER_PAIR, SMS * MUFU_LANES * f / MUFU_OPS_PER_PAIR)
 
 
@@ -308,14 +313,15 @@ def run_form(pkg, torch, w, precision, steps, warmup, graph=False, mode=0):
     """Time one form on one workload; returns a dict with value, kernel time and work."""
     with pkg.FsbmCoal(w.cfg(), precision=precision, mode=mode) as fc:
         ds = fc.upload(w.state(copy=False))
-        fc.autotune(ds)
+        fc.autotune(ds, w.dt, w.n_steps)
         fc.set_graph(graph)
         fc.set_timing(True)
         ms, st = time_steps(fc, ds, w, steps, warmup, fc.stream, torch)
     n_active = st["n_active"]
     pairs = pairs_per_active(w)
     out = dict(value=n_active * w.n_steps * steps / (ms / 1e3), ms_per_step=ms / steps, n_active=n_active,
-               pairs_per_s=pairs * w.n_steps * steps / (ms / 1e3))
+               points=w.n_points, collision_steps_per_call=w.n_steps, bin_pairs_per_step=pairs,
+               pairs_per_s=pairs * w.n_steps * steps / (ms / 1e3), timed_calls=steps, warmup_calls=warmup)
     if st["coal_launches"]:
         out["coal_ms"] = st["coal_ms"] / st["coal_launches"]
     elif st["steps_timed"]:
@@ -416,7 +422,8 @@ def _replica_child(rank, R, args_d, barrier, q):
     import paper_2409_07232_gb300 as pkg
     w = replica_workload(args_d, rank, R)
     precision = pkg.FSBM_FP64 if args_d["precision"] == "fp64" else pkg.FSBM_FP32_SPLIT
-    with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
+    mode = pkg.FSBM_SWEEP if args.mode == "sweep" else pkg.FSBM_PAIRWISE
+    with pkg.FsbmCoal(w.cfg(), precision=precision, mode=mode) as fc:
         ds = fc.upload(w.state(copy=False))
         fc.set_block(256)
         for _ in range(args_d["warmup"]):
@@ -560,6 +567,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["conus", "stress", "ragged"], default="conus")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--mode", choices=["pairwise", "sweep"], default="pairwise",
+                    help="sweep: Bott's in-place order (FP64 only; for profiling runs, not the bench line)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32 and 264-bin side measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--table", action="store_true",
@@ -604,9 +613,10 @@ def main():
     w = build_workload(args.workload, args.points)  # the same batch on every rank
     cost = w.pairs_per_step()
 
-    with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
+    mode = pkg.FSBM_SWEEP if args.mode == "sweep" else pkg.FSBM_PAIRWISE
+    with pkg.FsbmCoal(w.cfg(), precision=precision, mode=mode) as fc:
         ds = fc.upload(w.state(copy=False))
-        fc.autotune(ds)  # picks the CTA size on a copy of a sample of the batch
+        fc.autotune(ds, w.dt, w.n_steps)  # the CTA size, on a copy of a sample, at this call's shape
         fc.set_timing(True)
         with Clocks(local) as clk:
             ms, st = time_steps(fc, ds, w, args.steps, args.warmup, fc.stream, torch, barrier, shard=(rank, world))
@@ -631,13 +641,17 @@ def main():
         d2h = pinned["spectra"].nbytes + out_bytes
         fc.step_host(pinned, w.dt, w.n_steps)  # first call sizes the device mirrors
         barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
+        e2e_steps = min(args.steps, 5)  # each call copies the whole batch in and out (synchronous)
+        e2e_calls = []
+        for _ in range(e2e_steps):
+            t0 = time.perf_counter()
             fc.step_host(pinned, w.dt, w.n_steps)
-        e2e_s = time.perf_counter() - t0
+            e2e_calls.append(time.perf_counter() - t0)
+        e2e_s = sum(e2e_calls)
         barrier()
 
     ms_max, e2e_max = aggregate_times([ms, e2e_s], dist, device="cuda")
+    e2e_units = n_active * w.n_steps * e2e_steps
     h2d_all, d2h_all = aggregate_sums([h2d, d2h], dist, device="cuda")
     # every active point of the batch is stepped by exactly one rank
     units = n_active * w.n_steps * args.steps
@@ -674,8 +688,11 @@ def main():
                            "shards, one per GPU, no exchange (independent points)",
         },
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
-        "e2e": {"value": units / e2e_max, "unit": "grid-point coal updates/s", "h2d_bytes_per_step": h2d_all,
-                "d2h_bytes_per_step": d2h_all},
+        "e2e": {"value": e2e_units / e2e_max, "unit": "grid-point coal updates/s", "h2d_bytes_per_step": h2d_all,
+                "d2h_bytes_per_step": d2h_all, "steps": e2e_steps,
+                "seconds_per_call": {"min": min(e2e_calls), "median": statistics.median(e2e_calls),
+                                     "max": max(e2e_calls)},
+                "path": "fsbm_coal_step_host, pinned host buffers, copies in and out inside every call"},
         "gpu_launches": (4 if world == 1 else 5) * args.steps,
         "block_dim": st["block_dim"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
@@ -695,13 +712,20 @@ def main():
             value=value, ms_per_step=ms_max / args.steps, coal_ms=coal_ms,
             pairs_per_s=n_pairs * w.n_steps * args.steps / (ms_max / 1e3))
         import synth
-        st32 = synth.config5(n_points=20_000, seed=5001)
-        r32 = run_form(pkg, torch, st32, pkg.FSBM_FP32_SPLIT, 2, 3, graph=True)
-        st64 = synth.subset(st32, np.arange(1000))
-        r64 = run_form(pkg, torch, st64, pkg.FSBM_FP64, 1, 3)
-        # the ragged batch: 33 to 264 bins (four grids), 1 to 5 species, tau = 1e-12
-        rag = synth.config4(n_points=200_000, seed=4001)
-        rrag = run_form(pkg, torch, rag, pkg.FSBM_FP32_SPLIT, 2, 3, graph=True)
+        # the 264-bin 5-species stress points: FP32 on 100k and FP64 on 4k of the 500k (points
+        # are independent; the rate is per point)
+        st32 = synth.config5(n_points=100_000, seed=5001)
+        r32 = run_form(pkg, torch, st32, pkg.FSBM_FP32_SPLIT, 1, 2, graph=True)
+        st64 = synth.subset(st32, np.arange(4000))
+        r64 = run_form(pkg, torch, st64, pkg.FSBM_FP64, 1, 2)
+        # the ragged batch: 2M points, 33 to 264 bins (four grids), 1 to 5 species, tau = 1e-12
+        rag = synth.config4(n_points=2_000_000, seed=4001)
+        rrag = run_form(pkg, torch, rag, pkg.FSBM_FP32_SPLIT, 1, 2, graph=True)
+        del rag
+        # configs 1 and 3: 1024 single-species 33-bin points, Golovin kernel, dt = 1 s x 100
+        c1 = synth.config1()
+        rc1 = run_form(pkg, torch, c1, pkg.FSBM_FP64, 2, 3)
+        rc3 = run_form(pkg, torch, c1, pkg.FSBM_FP32_SPLIT, 2, 3, graph=True)
         # Bott's in-place order (SWEEP), FP64, one thread per point, on a sample of the domain
         sw = synth.conus_sample(20_000, 0, seed=8)
         rsw = run_form(pkg, torch, sw, pkg.FSBM_FP64, 1, 3, mode=pkg.FSBM_SWEEP)
@@ -718,18 +742,23 @@ def main():
         for R in (2, 4):
             forms[f"conus_33bin_fp32_split_replicas_streams_{R}"] = run_replicas_form(
                 pkg, torch, w, pkg.FSBM_FP32_SPLIT, R, 2, 3)
-        for key, rr, ww, pr in (("stress_264bin_fp32_split_graph", r32, st32, 1),
-                                ("stress_264bin_fp64", r64, st64, 0),
-                                ("ragged_33to264bin_fp32_split_graph", rrag, rag, 1),
+        for key, rr, ww, pr in (("stress_264bin_fp32_split_graph_100k", r32, st32, 1),
+                                ("stress_264bin_fp64_4k", r64, st64, 0),
+                                ("ragged_33to264bin_fp32_split_graph_2M", rrag, None, 1),
+                                ("config1_33bin_fp64_golovin", rc1, c1, 0),
+                                ("config3_33bin_fp32_split_graph_golovin", rc3, c1, 1),
                                 ("conus_33bin_fp64_sweep_20k", rsw, sw, 0),
                                 ("conus_33bin_fp32_split_graph_two_levels", rlv32, lv32, 1),
                                 ("conus_33bin_fp64_two_levels_50k", rlv64, lv64, 0)):
-            rr["points"] = ww.n_points
             kms = rr.get("coal_ms") or rr.get("step_ms_graph")
-            if "sweep" in key:  # another algorithm (CUDA's log/exp/expm1, divisions): no pair-op model
-                rr["alu_frac"] = None
+            pairs, nst = rr["bin_pairs_per_step"], rr["collision_steps_per_call"]
+            if "sweep" in key:  # another algorithm: CUDA's log/exp/expm1 and IEEE divisions per pair
+                rr["alu_frac"] = ((pairs * nst / (kms / 1e3)) /
+                                  alu_peak_pairs(0, sm_mhz, SWEEP_FP64_OPS_PER_PAIR)) if SWEEP_FP64_OPS_PER_PAIR else None
+                rr["peak_basis"] = "FP64 pipe %d/clk/SM / %s FP64 ops per pair (ncu-counted)" % (
+                    FP64_PER_CLK, SWEEP_FP64_OPS_PER_PAIR)
             else:
-                rr["alu_frac"] = (pairs_per_active(ww) * ww.n_steps / (kms / 1e3)) / alu_peak_pairs(pr, sm_mhz)
+                rr["alu_frac"] = (pairs * nst / (kms / 1e3)) / alu_peak_pairs(pr, sm_mhz)
             if "ragged" in key:
                 rr["pairs_basis"] = "every bin of every stored species; the 1e-12 range cut-off skips some"
             forms[key] = rr

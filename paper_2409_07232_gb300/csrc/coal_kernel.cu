@@ -233,47 +233,40 @@ struct Smem {
   T* lam;         // [S][nmax]
   T* xs;          // [nmax]
   T* cd;          // [nmax] Courant number per bin distance
-  T* llam;        // [S*nmax] the limited rows' ratios, in row order
-  T* lN;          // [S*nmax] their number concentrations
-  int* lim;       // [S*nmax] rows whose limiter ratio is below 1, ascending row index
-  int* loff;      // [S*nmax] Kr offset (species id of the row's species, bin) of those rows
+  T* llam;        // [S*nmax + 8] ratios of the listed columns (limited rows), padded to 8
+  T* lN;          // [S*nmax + 8] number concentrations of the listed columns, padded to 8
+  int* lim;       // [S*nmax + 8] rows whose limiter ratio is below 1, ascending row index
+  int* loff;      // [S*nmax + 8] Kr offset (species, bin) of the listed columns, padded to 8
+  // every array starts on a 16-byte boundary (the column lists are read four entries at a time)
+  static __host__ __device__ size_t up16(size_t b) { return (b + 15) & ~size_t(15); }
   static __host__ __device__ size_t bytes(int nmax, int S) {
-    size_t b = sizeof(double) * 2 * S * nmax + sizeof(Sum) * 2 * S * S * nmax;
-    if (sizeof(T) != sizeof(double)) b += sizeof(T) * S * nmax;
-    b += sizeof(T) * (4 * S * nmax + 2 * nmax) + sizeof(int) * 2 * S * nmax;
-    return (b + 15) & ~size_t(15);
+    const size_t e = (size_t)S * nmax, l = e + 8;
+    size_t b = 2 * up16(sizeof(double) * e) + 2 * up16(sizeof(Sum) * S * e);
+    if (sizeof(T) != sizeof(double)) b += up16(sizeof(T) * e);
+    b += 2 * up16(sizeof(T) * e) + 2 * up16(sizeof(T) * nmax) + 2 * up16(sizeof(T) * l) + 2 * up16(sizeof(int) * l);
+    return b;
   }
   __device__ void carve(unsigned char* base, int nmax, int S) {
+    const size_t e = (size_t)S * nmax, l = e + 8;
     unsigned char* p = base;
-    M = reinterpret_cast<double*>(p);
-    p += sizeof(double) * S * nmax;
-    loss = reinterpret_cast<double*>(p);
-    p += sizeof(double) * S * nmax;
-    stay = reinterpret_cast<Sum*>(p);
-    p += sizeof(Sum) * S * S * nmax;
-    up = reinterpret_cast<Sum*>(p);
-    p += sizeof(Sum) * S * S * nmax;
-    if (sizeof(T) != sizeof(double)) {
-      Mt = reinterpret_cast<T*>(p);
-      p += sizeof(T) * S * nmax;
-    } else {
-      Mt = reinterpret_cast<T*>(M);
-    }
-    N = reinterpret_cast<T*>(p);
-    p += sizeof(T) * S * nmax;
-    lam = reinterpret_cast<T*>(p);
-    p += sizeof(T) * S * nmax;
-    xs = reinterpret_cast<T*>(p);
-    p += sizeof(T) * nmax;
-    cd = reinterpret_cast<T*>(p);
-    p += sizeof(T) * nmax;
-    llam = reinterpret_cast<T*>(p);
-    p += sizeof(T) * S * nmax;
-    lN = reinterpret_cast<T*>(p);
-    p += sizeof(T) * S * nmax;
-    lim = reinterpret_cast<int*>(p);
-    p += sizeof(int) * S * nmax;
-    loff = reinterpret_cast<int*>(p);
+    auto take = [&](size_t nbytes) {
+      unsigned char* q = p;
+      p += up16(nbytes);
+      return q;
+    };
+    M = reinterpret_cast<double*>(take(sizeof(double) * e));
+    loss = reinterpret_cast<double*>(take(sizeof(double) * e));
+    stay = reinterpret_cast<Sum*>(take(sizeof(Sum) * S * e));
+    up = reinterpret_cast<Sum*>(take(sizeof(Sum) * S * e));
+    Mt = sizeof(T) != sizeof(double) ? reinterpret_cast<T*>(take(sizeof(T) * e)) : reinterpret_cast<T*>(M);
+    N = reinterpret_cast<T*>(take(sizeof(T) * e));
+    lam = reinterpret_cast<T*>(take(sizeof(T) * e));
+    xs = reinterpret_cast<T*>(take(sizeof(T) * nmax));
+    cd = reinterpret_cast<T*>(take(sizeof(T) * nmax));
+    llam = reinterpret_cast<T*>(take(sizeof(T) * l));
+    lN = reinterpret_cast<T*>(take(sizeof(T) * l));
+    lim = reinterpret_cast<int*>(take(sizeof(int) * l));
+    loff = reinterpret_cast<int*>(take(sizeof(int) * l));
   }
 };
 
@@ -625,71 +618,106 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       }
       __syncthreads();
 
-      // 2. requested loss R and limiter ratios (one lane per row (a, i); Kr is i-fastest, so
-      //    a warp's loads of one column are contiguous). Each lane keeps eight partial sums
-      //    (columns j .. j+7) so that eight loads are in flight at once; the partials are
-      //    added in a fixed order.
+      // 2. requested loss R and limiter ratios. The active columns (species b, bin j) are
+      //    listed once in shared memory as (Kr offset, N), padded with zero entries to a
+      //    multiple of 8; Kr is i-fastest, so for a fixed column the rows' entries are
+      //    contiguous and the offset (b, j) is the same for every row. One item per (row,
+      //    run of the list) keeps eight partial sums (eight loads in flight) and parks its sum
+      //    in the gain arrays (free until the gain pass); then one lane per row adds its runs
+      //    in order and forms R and lambda in FP64.
+      using Sum = typename Num<T>::Sum;
+      Sum* const part = sm.stay;  // [run][E] partial row sums; the correction's runs reach into
+                                  // sm.up, which follows sm.stay
+      bool limited = false;
+      const unsigned inv_E = (unsigned)(0x100000000ull / (unsigned long long)E + 1);
       const T* __restrict__ Kr = Sel<T>::Kr(G);
       const T* __restrict__ Krd = lev ? Sel<T>::Kr_d(G) : nullptr;
-      bool fired = false;
-      for (int r = tid; r < E; r += NT) {
-        const int a = div_n(r, G.inv_n), i = r - a * n;
-        double R = 0.0;
-        double lamd = 1.0;
-        if (i >= s_lo[a] && i <= s_hi[a]) {
+      int NC = 0;  // active columns, then padded to a multiple of 8
+      for (int b = 0; b < ns; ++b) NC += max(0, s_hi[b] - s_lo[b] + 1);
+      const int NCp = (NC + 7) & ~7;
+      for (int e = tid; e < max(E, NCp); e += NT) {
+        if (e < E) {
+          const int b = div_n(e, G.inv_n), j = e - b * n;
+          if (j >= s_lo[b] && j <= s_hi[b]) {
+            int pos = j - s_lo[b];
+            for (int b2 = 0; b2 < b; ++b2) pos += max(0, s_hi[b2] - s_lo[b2] + 1);
+            sm.loff[pos] = (s_sp[b] * n + j) * n;
+            sm.lN[pos] = sm.N[e];
+          }
+        }
+        if (e >= NC && e < NCp) {
+          sm.loff[e] = 0;
+          sm.lN[e] = T(0);
+        }
+      }
+      __syncthreads();
+      {
+        const int nch = max(1, min((NCp + 31) / 32, ns));
+        const int span = (((NCp + nch - 1) / nch) + 7) & ~7;
+        for (int it = tid; it < nch * E; it += NT) {
+          const int ch = (int)__umulhi((unsigned)it, inv_E), r = it - ch * E;
+          const int a = div_n(r, G.inv_n), i = r - a * n;
           Acc<T> acc;
-          for (int b = 0; b < ns; ++b) {
-            const size_t base = (size_t)(s_sp[a] * S + s_sp[b]) * n * n + i;
-            if (FSBM_CHECKED_BUILD && s_lo[b] <= s_hi[b] &&
-                !(FSBM_OK(t.chk, s_lo[b], n) && FSBM_OK(t.chk, base + (size_t)s_hi[b] * n, (size_t)S * S * n * n)))
-              continue;
-            const T* __restrict__ Kab = Kr + base;
-            const T* __restrict__ Kabd = lev ? Krd + base : nullptr;
-            const T* __restrict__ Nb = sm.N + b * n;
-            for (int j0 = s_lo[b]; j0 <= s_hi[b]; j0 += kLossRun) {
-              const int j1 = min(s_hi[b], j0 + kLossRun - 1);
+          if (i >= s_lo[a] && i <= s_hi[a] &&
+              (!FSBM_CHECKED_BUILD || (FSBM_OK(t.chk, s_sp[a], S) && FSBM_OK(t.chk, nch * E - 1, S * S * nmax)))) {
+            const T* __restrict__ Krow = Kr + (size_t)s_sp[a] * S * n * n + i;
+            const T* __restrict__ Krowd = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
+            const int qa = ch * span, qb = min(NCp, qa + span);
+            for (int q0 = qa; q0 < qb; q0 += 32) {
+              const int q1 = min(qb, q0 + 32);
               T p[8];
 #pragma unroll
               for (int u = 0; u < 8; ++u) p[u] = T(0);
-              int j = j0;
-              for (; j + 7 <= j1; j += 8) {
+              for (int q = q0; q < q1; q += 8) {
+                const int4 oa = *reinterpret_cast<const int4*>(sm.loff + q);
+                const int4 ob = *reinterpret_cast<const int4*>(sm.loff + q + 4);
+                const int o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
                 T kk[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) kk[u] = __ldg(Kab + (size_t)(j + u) * n);
+                for (int u = 0; u < 8; ++u) kk[u] = __ldg(Krow + o[u]);
                 if (lev) {
 #pragma unroll
-                  for (int u = 0; u < 8; ++u) kk[u] = fma(wT, __ldg(Kabd + (size_t)(j + u) * n), kk[u]);
+                  for (int u = 0; u < 8; ++u) kk[u] = fma(wT, __ldg(Krowd + o[u]), kk[u]);
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) p[u] = fma(kk[u], Nb[j + u], p[u]);
-              }
-              for (; j <= j1; ++j) {
-                T k0 = __ldg(Kab + (size_t)j * n);
-                if (lev) k0 = fma(wT, __ldg(Kabd + (size_t)j * n), k0);
-                p[0] = fma(k0, Nb[j], p[0]);
+                for (int u = 0; u < 8; ++u) p[u] = fma(kk[u], sm.lN[q + u], p[u]);
               }
               acc.add(((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
               acc.flush();
             }
           }
-          R = dt * sm.M[r] * Num<T>::val(acc.sum());
-          if (R > sm.M[r]) {  // lambda = M / R < 1 (R > 0 here)
-            lamd = sm.M[r] / R;
-            fired = true;
-          }
+          part[it] = acc.sum();
         }
-        sm.loss[r] = R;
-        sm.lam[r] = (T)lamd;
+        __syncthreads();
+        bool fired = false;
+        for (int r = tid; r < E; r += NT) {
+          const int a = div_n(r, G.inv_n), i = r - a * n;
+          double R = 0.0;
+          double lamd = 1.0;
+          if (i >= s_lo[a] && i <= s_hi[a]) {
+            Sum tot = part[r];
+            for (int ch = 1; ch < nch; ++ch) Num<T>::add(tot, part[ch * E + r]);
+            R = dt * sm.M[r] * Num<T>::val(tot);
+            if (R > sm.M[r]) {  // lambda = M / R < 1 (R > 0 here)
+              lamd = sm.M[r] / R;
+              fired = true;
+            }
+          }
+          sm.loss[r] = R;
+          sm.lam[r] = (T)lamd;
+        }
+        if (tid == 0) s_task = 0;
+        limited = __syncthreads_or(fired);
       }
-      if (tid == 0) s_task = 0;
-      const bool limited = __syncthreads_or(fired);
       if (limited) status |= 1;
 
       // 3. limited losses: loss_i = dt M_i sum_j K N_j min(lam_i, lam_j)
       //      = lam_i R_i + dt M_i sum_{j limited} K N_j (min(lam_i, lam_j) - lam_i),
       //    where lam_i R_i = M_i when lam_i < 1 and every term with lam_j >= lam_i is 0. The
-      //    sum runs over the rows whose ratio fired, gathered once in row order; each row
-      //    walks that list with eight partial sums, added in a fixed order.
+      //    limited rows are listed in row order as columns (Kr offset, N, lambda), padded with
+      //    zero entries to a multiple of 8; one item per (row, run of the list), at most 2 ns
+      //    runs per row so that the items fit in the gain arrays; then one lane per row adds
+      //    its runs in order.
       if (limited) {
         if (warp == 0) {
           int cnt = 0;
@@ -704,53 +732,71 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           if (lane == 0) s_nlim = cnt;
         }
         __syncthreads();
-        const int L = s_nlim;
-        for (int q = tid; q < L; q += NT) {
-          const int r = sm.lim[q];
-          const int b = div_n(r, G.inv_n), j = r - b * n;
-          sm.llam[q] = sm.lam[r];
-          sm.lN[q] = sm.N[r];
-          sm.loff[q] = (s_sp[b] * n + j) * n;
-          if (FSBM_CHECKED_BUILD && !FSBM_OK(t.chk, (size_t)(S - 1) * S * n * n + (n - 1) + sm.loff[q], (size_t)S * S * n * n))
+        const int L = s_nlim, Lp = (L + 7) & ~7;
+        for (int q = tid; q < Lp; q += NT) {
+          if (q < L) {
+            const int r = sm.lim[q];
+            const int b = div_n(r, G.inv_n), j = r - b * n;
+            sm.llam[q] = sm.lam[r];
+            sm.lN[q] = sm.N[r];
+            sm.loff[q] = (s_sp[b] * n + j) * n;
+          } else {
+            sm.llam[q] = T(1);
+            sm.lN[q] = T(0);
             sm.loff[q] = 0;
+          }
+        }
+        __syncthreads();
+        const int nch = max(1, min((Lp + 31) / 32, 2 * ns));
+        const int span = (((Lp + nch - 1) / nch) + 7) & ~7;
+        for (int it = tid; it < nch * E; it += NT) {
+          const int ch = (int)__umulhi((unsigned)it, inv_E), r = it - ch * E;
+          const int a = div_n(r, G.inv_n), i = r - a * n;
+          Acc<T> acc;
+          if (i >= s_lo[a] && i <= s_hi[a] &&
+              (!FSBM_CHECKED_BUILD || (FSBM_OK(t.chk, s_sp[a], S) && FSBM_OK(t.chk, L, E + 1) &&
+                                       FSBM_OK(t.chk, nch * E - 1, 2 * S * S * nmax)))) {
+            const T li = sm.lam[r];
+            const T* __restrict__ Krow = Kr + (size_t)s_sp[a] * S * n * n + i;
+            const T* __restrict__ Krowd = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
+            const int qa = ch * span, qb = min(Lp, qa + span);
+            for (int q0 = qa; q0 < qb; q0 += 32) {
+              const int q1 = min(qb, q0 + 32);
+              T p[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) p[u] = T(0);
+              for (int q = q0; q < q1; q += 8) {
+                const int4 oa = *reinterpret_cast<const int4*>(sm.loff + q);
+                const int4 ob = *reinterpret_cast<const int4*>(sm.loff + q + 4);
+                const int o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+                T kk[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) kk[u] = __ldg(Krow + o[u]);
+                if (lev) {
+#pragma unroll
+                  for (int u = 0; u < 8; ++u) kk[u] = fma(wT, __ldg(Krowd + o[u]), kk[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                  p[u] = fma((min_nonneg(li, sm.llam[q + u]) - li) * kk[u], sm.lN[q + u], p[u]);
+              }
+              acc.add(((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
+              acc.flush();
+            }
+          }
+          part[it] = acc.sum();
         }
         __syncthreads();
         for (int r = tid; r < E; r += NT) {
           const int a = div_n(r, G.inv_n), i = r - a * n;
           if (i < s_lo[a] || i > s_hi[a]) continue;
+          Sum tot = Num<T>::zero();
+          for (int ch = 0; ch < nch; ++ch) Num<T>::add(tot, part[ch * E + r]);
           const T li = sm.lam[r];
-          if (FSBM_CHECKED_BUILD && !(FSBM_OK(t.chk, s_sp[a], S) && FSBM_OK(t.chk, L, E + 1))) continue;
-          const T* __restrict__ Kri = Kr + (size_t)s_sp[a] * S * n * n + i;
-          const T* __restrict__ Krid = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
-          Acc<T> acc;
-          for (int q0 = 0; q0 < L; q0 += kLossRun) {
-            const int q1 = min(L, q0 + kLossRun);
-            T p[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) p[u] = T(0);
-            int q = q0;
-            for (; q + 7 < q1; q += 8) {
-              T kk[8];
-#pragma unroll
-              for (int u = 0; u < 8; ++u) kk[u] = __ldg(Kri + sm.loff[q + u]);
-              if (lev) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) kk[u] = fma(wT, __ldg(Krid + sm.loff[q + u]), kk[u]);
-              }
-#pragma unroll
-              for (int u = 0; u < 8; ++u) p[u] = fma((min_nonneg(li, sm.llam[q + u]) - li) * kk[u], sm.lN[q + u], p[u]);
-            }
-            for (; q < q1; ++q) {
-              T k0 = __ldg(Kri + sm.loff[q]);
-              if (lev) k0 = fma(wT, __ldg(Krid + sm.loff[q]), k0);
-              p[0] = fma((min_nonneg(li, sm.llam[q]) - li) * k0, sm.lN[q], p[0]);
-            }
-            acc.add(((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
-            acc.flush();
-          }
           const double base = li < T(1) ? sm.M[r] : sm.loss[r];
-          sm.loss[r] = base + dt * sm.M[r] * Num<T>::val(acc.sum());
+          sm.loss[r] = base + dt * sm.M[r] * Num<T>::val(tot);
         }
+        __syncthreads();  // the partial sums live in the gain arrays
       }
 
       // 4. gains. Lanes run over the flattened list of (target bin 1..n-2, orientation)

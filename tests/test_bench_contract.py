@@ -77,3 +77,14 @@ def test_replica_slabs_partition_the_domain():
     assert sum(p.n_points for p in parts) == whole.n_points
     assert np.array_equal(np.concatenate([p.spectra for p in parts]), whole.spectra)
     assert np.array_equal(np.concatenate([p.cloudy for p in parts]), whole.cloudy)
+
+
+def test_contiguous_slabs_equal_the_subset_copies():
+    import synth
+    w = synth.conus_sample(200, 50, seed=3)
+    edges = [0, 37, 120, w.n_points]
+    for a, b in zip(edges[:-1], edges[1:]):
+        s, c = bench.slab(w, a, b), synth.subset(w, np.arange(a, b))
+        assert s.n_points == c.n_points == b - a
+        assert np.array_equal(s.spectra, c.spectra) and np.array_equal(s.offset, c.offset)
+        assert np.array_equal(s.species_mask, c.species_mask) and np.array_equal(s.cloudy, c.cloudy)
