@@ -45,11 +45,6 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 __device__ __forceinline__ int warp_min_i(int v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -417,12 +412,19 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
       for (int dc = d0; dc <= d1; dc += kGainRun) {
         const int dce = min(d1, dc + kGainRun - 1);
         int d = dc;
-        if (sizeof(T) == sizeof(float) && !LEVELS) {
+        if (sizeof(T) == sizeof(float)) {
           // FP32: two pairs per iteration, so that two flux chains (each a string of dependent
-          // SFU and FMA operations) are in flight per lane; the sums take them in pair order
+          // SFU and FMA operations) are in flight per lane; the sums take them in pair order.
+          // (FP64 runs one pair at a time: its double-precision pipe is already the bound, and
+          // the unrolled form measured slower there.)
           for (; d + 1 <= dce; d += 2, Kp += 2 * kstride) {
             const int i = m - d;
-            const T K0 = __ldg(Kp), K1 = __ldg(Kp + kstride);
+            T K0 = __ldg(Kp), K1 = __ldg(Kp + kstride);
+            if (LEVELS) {
+              K0 = fma(wl, __ldg(Kq), K0);
+              K1 = fma(wl, __ldg(Kq + kstride), K1);
+              Kq += 2 * kstride;
+            }
             T dM0 = K0 * am * Ns[i], dM1 = K1 * am * Ns[i - 1];
             if (LIMITED) {
               dM0 *= min_nonneg(Ls[i], ll);
@@ -652,7 +654,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       }
       __syncthreads();
       {
-        const int nch = max(1, min((NCp + 31) / 32, ns));
+        const int nch = max(1, min((NCp + kLossRun - 1) / kLossRun, ns));
         const int span = (((NCp + nch - 1) / nch) + 7) & ~7;
         for (int it = tid; it < nch * E; it += NT) {
           const int ch = (int)__umulhi((unsigned)it, inv_E), r = it - ch * E;
@@ -663,8 +665,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
             const T* __restrict__ Krow = Kr + (size_t)s_sp[a] * S * n * n + i;
             const T* __restrict__ Krowd = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
             const int qa = ch * span, qb = min(NCp, qa + span);
-            for (int q0 = qa; q0 < qb; q0 += 32) {
-              const int q1 = min(qb, q0 + 32);
+            for (int q0 = qa; q0 < qb; q0 += kLossRun) {
+              const int q1 = min(qb, q0 + kLossRun);
               T p[8];
 #pragma unroll
               for (int u = 0; u < 8; ++u) p[u] = T(0);
@@ -747,7 +749,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           }
         }
         __syncthreads();
-        const int nch = max(1, min((Lp + 31) / 32, 2 * ns));
+        const int nch = max(1, min((Lp + kLossRun - 1) / kLossRun, 2 * ns));
         const int span = (((Lp + nch - 1) / nch) + 7) & ~7;
         for (int it = tid; it < nch * E; it += NT) {
           const int ch = (int)__umulhi((unsigned)it, inv_E), r = it - ch * E;
@@ -760,8 +762,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
             const T* __restrict__ Krow = Kr + (size_t)s_sp[a] * S * n * n + i;
             const T* __restrict__ Krowd = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
             const int qa = ch * span, qb = min(Lp, qa + span);
-            for (int q0 = qa; q0 < qb; q0 += 32) {
-              const int q1 = min(qb, q0 + 32);
+            for (int q0 = qa; q0 < qb; q0 += kLossRun) {
+              const int q1 = min(qb, q0 + kLossRun);
               T p[8];
 #pragma unroll
               for (int u = 0; u < 8; ++u) p[u] = T(0);

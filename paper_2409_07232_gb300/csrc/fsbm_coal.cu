@@ -801,8 +801,11 @@ fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
   if (st != FSBM_OK) return st;
   c->tune_cache_hit = 0;
   if (n_points == 0) return FSBM_OK;
-  // A sample of up to 2^16 points runs the caller's steps per candidate: long enough that the
-  // per-point start-up work and the last points' tail weigh about as much as in a real call.
+  // The first 2^16 points (all if fewer) give the batch's class mix; the timed sample is a
+  // prefix of them holding about kTuneWork pair updates at the caller's dt and up to 4 of its
+  // steps (at least 2432 points, several per resident CTA, so that the last points' tail
+  // weighs about as much as in a real call), which keeps a tuning call near 0.1 s per
+  // candidate for any grid.
   const int64_t P = std::min<int64_t>(n_points, 1 << 16);
   int64_t off[2];
   CU(c, cudaMemcpyAsync(&off[0], s->offset, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
@@ -842,8 +845,25 @@ fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
     return cuda_fail(c, ce, who);
   }
   int32_t cls_count[kNumBuckets] = {};
-  for (int r = 0; r < n_cls; ++r) cls_count[r] = first[r + 1] - first[r];
+  double work = 0.0, act = 0.0;
+  for (int r = 0; r < n_cls; ++r) {
+    cls_count[r] = first[r + 1] - first[r];
+    work += (double)cls_count[r] * (double)c->t.rank_cost[r];
+    act += cls_count[r];
+  }
   const std::string key = tune_key(c, dt, n_steps, cls_count, n_cls, P);
+  const int tune_steps = std::min(n_steps, 4);
+  const double kTuneWork = c->precision == FSBM_FP64 ? 1.5e9 : 3e10;  // pair updates per run
+  const double per_point = work / (double)P;  // pair updates per step per sample point (clear ones cost 0)
+  const int64_t Pt = std::max<int64_t>(
+      std::min<int64_t>(P, 2432), std::min<int64_t>(P, (int64_t)(kTuneWork / std::max(per_point * tune_steps, 1.0))));
+  size_t tbytes = bytes;
+  if (Pt < P) {
+    int64_t offt = 0;
+    CU(c, cudaMemcpyAsync(&offt, s->offset + Pt, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+    tbytes = (size_t)(offt - off[0]) * esz;
+  }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -855,6 +875,9 @@ fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
       return ensure_plan(c);
     }
   }
+  PointsDev pt = p;  // the timed sample: the first Pt points of the copy
+  pt.n_points = Pt;
+  c->scratch.n_blocks = (Pt + kCompactThreads - 1) / kCompactThreads;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -868,10 +891,10 @@ fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
     if (coal_plan(c->t, c->precision, b, c->n_sms, &plan) != cudaSuccess) continue;
     float ms_tot = 0.f;
     for (int rep = 0; rep < 2; ++rep) {
-      cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
-      launch_compact(c->t, p, P, c->scratch, c->stream);
+      cudaMemcpyAsync(tmp, src, tbytes, cudaMemcpyDeviceToDevice, c->stream);
+      launch_compact(c->t, pt, Pt, c->scratch, c->stream);
       cudaEventRecord(e0, c->stream);
-      launch_coal(c->t, c->precision, p, c->scratch, dt, n_steps, plan, c->stream);
+      launch_coal(c->t, c->precision, pt, c->scratch, dt, tune_steps, plan, c->stream);
       cudaEventRecord(e1, c->stream);
       cudaEventSynchronize(e1);
       float ms = 0.f;
