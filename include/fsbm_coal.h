@@ -298,6 +298,14 @@ FSBM_API fsbm_status fsbm_coal_set_graph(fsbm_coal_ctx* ctx, int32_t enable);
  * autotuner's tests. Valid sizes: 32, 64, 128, 256, 512. */
 FSBM_API fsbm_status fsbm_coal_set_block(fsbm_coal_ctx* ctx, int32_t block_dim);
 
+/* Lanes that share one gain item's bin pairs in the pairwise kernels: 1, 2, 4 or 8, or 0
+ * (the default) for the library's rule, which gives a point whose gain items would fill fewer
+ * than four warps (one or two species on a short grid) up to 8 lanes per item and every other
+ * point one. The lanes take every P-th bin distance and their partial sums are added in a
+ * fixed order, so results depend on this setting (to rounding) but never on the CTA size.
+ * Ignored by SWEEP. Returns FSBM_E_ARG for any other value. */
+FSBM_API fsbm_status fsbm_coal_set_gain_split(fsbm_coal_ctx* ctx, int32_t lanes);
+
 /* Enable (1) or disable (0, the default) CUDA-event timing of the collision kernel and of
  * whole steps; fsbm_coal_get_stats returns the totals. Costs two event records per step. */
 FSBM_API fsbm_status fsbm_coal_set_timing(fsbm_coal_ctx* ctx, int32_t enable);

@@ -31,6 +31,7 @@ from .binding import (  # noqa: F401
     fsbm_coal_last_error,
     fsbm_coal_math_check,
     fsbm_coal_set_block,
+    fsbm_coal_set_gain_split,
     fsbm_coal_set_graph,
     fsbm_coal_set_timing,
     fsbm_coal_shard_bounds,
@@ -162,6 +163,9 @@ class FsbmCoal:
 
     def set_block(self, block_dim: int) -> None:
         fsbm_coal_set_block(self.ctx, block_dim)
+
+    def set_gain_split(self, lanes: int) -> None:
+        fsbm_coal_set_gain_split(self.ctx, lanes)
 
     def set_timing(self, enable: bool) -> None:
         fsbm_coal_set_timing(self.ctx, enable)

@@ -41,7 +41,7 @@ _STATUS_NAMES = {0: "FSBM_OK", -1: "FSBM_E_ARG", -2: "FSBM_E_CUDA", -3: "FSBM_E_
 # Every entry point include/fsbm_coal.h declares.
 EXPORTS = ("fsbm_coal_init", "fsbm_coal_clone", "fsbm_coal_step", "fsbm_coal_step_host", "fsbm_coal_step_noalloc", "fsbm_coal_step_wrf",
            "fsbm_coal_step_shard", "fsbm_coal_shard_bounds", "fsbm_coal_autotune", "fsbm_coal_autotune_steps",
-           "fsbm_coal_set_graph", "fsbm_coal_set_block", "fsbm_coal_set_timing", "fsbm_coal_get_stats",
+           "fsbm_coal_set_graph", "fsbm_coal_set_block", "fsbm_coal_set_gain_split", "fsbm_coal_set_timing", "fsbm_coal_get_stats",
            "fsbm_coal_get_active_list", "fsbm_coal_math_check", "fsbm_coal_check_record", "fsbm_coal_destroy",
            "fsbm_coal_last_error")
 
@@ -155,6 +155,7 @@ def load(path: str = None):
                                          ctypes.c_int),
             "fsbm_coal_set_graph": ([V, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_set_block": ([V, ctypes.c_int32], ctypes.c_int),
+            "fsbm_coal_set_gain_split": ([V, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_set_timing": ([V, ctypes.c_int32], ctypes.c_int),
             "fsbm_coal_get_stats": ([V, P(fsbm_coal_stats)], ctypes.c_int),
             "fsbm_coal_get_active_list": ([V, V, ctypes.c_int64, P(ctypes.c_int64)], ctypes.c_int),
@@ -293,6 +294,10 @@ def fsbm_coal_set_graph(ctx, enable: bool) -> None:
 
 def fsbm_coal_set_block(ctx, block_dim: int) -> None:
     _check(ctx, load().fsbm_coal_set_block(ctx, int(block_dim)), "fsbm_coal_set_block")
+
+
+def fsbm_coal_set_gain_split(ctx, lanes: int) -> None:
+    _check(ctx, load().fsbm_coal_set_gain_split(ctx, int(lanes)), "fsbm_coal_set_gain_split")
 
 
 def fsbm_coal_set_timing(ctx, enable: bool) -> None:

@@ -214,6 +214,20 @@ template <> struct Acc<float> {
 };
 constexpr int kGainRun = 16;
 constexpr int kLossRun = 32;
+constexpr int kSplitLanes = 128;  // a point's gain items share lanes until they fill 4 warps
+
+// a += (a of lane ^ off), every lane of the warp taking part
+template <typename T>
+__device__ __forceinline__ void shfl_add(typename Num<T>::Sum& a, int off);
+template <>
+__device__ __forceinline__ void shfl_add<double>(double& a, int off) {
+  a += __shfl_xor_sync(0xffffffffu, a, off);
+}
+template <>
+__device__ __forceinline__ void shfl_add<float>(FF& a, int off) {
+  const FF b{__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
+  ff_add(a, b);
+}
 
 // Shared-memory carve-up for nmax bins and S species (T = pair-arithmetic type).
 template <typename T>
@@ -372,10 +386,12 @@ template <> struct TargetOf<float> {
 // its limiter ratio and the Courant number c(d); everything else is in registers.
 //   dM = C (x_i + x_m) = [K (1 + alpha^-d)] N_i [M_m dt]      (x_i = x_m alpha^-d)
 // LEVELS: the point lies between two pressure levels; its kernel is K1 + wl (K2 - K1).
+// SPLIT: the item's pairs are shared by P lanes; part p takes every P-th distance of each group
+// (d = d0 + p, d0 + p + P, ...), and the caller adds the P partial sums in a fixed order.
 template <typename T, bool LIMITED, bool LEVELS, bool TOP>
 __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T>& sm, const Orient& o_ref,
-                                          const int* lo, const int* hi, int k, bool on, T dt, double B,
-                                          const MathTabs& mt, T wl, typename Num<T>::Sum* out_stay,
+                                          const int* lo, const int* hi, int k, bool on, int p, int P, T dt,
+                                          double B, const MathTabs& mt, T wl, typename Num<T>::Sum* out_stay,
                                           typename Num<T>::Sum* out_up) {
   const int n = G.n;
   const Orient o = o_ref;  // register copy
@@ -392,7 +408,7 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
   if (FSBM_CHECKED_BUILD && on && !TOP && !FSBM_OK(G.chk, k + 1, n)) on = false;
   TargetOf<T> tgt;
   if (!TOP) tgt.init(on ? sm.Mt[o.c * n + k] : T(0), on ? sm.Mt[o.c * n + k + 1] : T(0), B, mt);
-  const int kstride = n * S2;
+  const int kstride = n * S2 * P;  // table step from one of this part's distances to the next
   for (int kap = 0; kap <= G.kappa_max; ++kap) {
     const int dlo = max(G.d_lo[kap], (int)o.dmin), dhi = G.d_hi[kap];
     const int m0 = max(TOP ? n - 1 - kap : k - kap, lo_l);
@@ -405,19 +421,19 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
         continue;
       const T am = Ml[m] * dt;
       const T ll = LIMITED ? Ll[m] : T(1);
-      const ptrdiff_t e0 = (ptrdiff_t)(d0 * n + m) * S2;
+      const ptrdiff_t e0 = (ptrdiff_t)((d0 + p) * n + m) * S2;
       const T* __restrict__ Kp = Kd + e0;
       const T* __restrict__ Kq = LEVELS ? Kdd + e0 : nullptr;
       // runs of up to kGainRun pairs, each folded into the running totals after it
-      for (int dc = d0; dc <= d1; dc += kGainRun) {
-        const int dce = min(d1, dc + kGainRun - 1);
+      for (int dc = d0 + p; dc <= d1; dc += kGainRun * P) {
+        const int dce = min(d1, dc + (kGainRun - 1) * P);
         int d = dc;
         if (sizeof(T) == sizeof(float)) {
           // FP32: two pairs per iteration, so that two flux chains (each a string of dependent
           // SFU and FMA operations) are in flight per lane; the sums take them in pair order.
           // (FP64 runs one pair at a time: its double-precision pipe is already the bound, and
           // the unrolled form measured slower there.)
-          for (; d + 1 <= dce; d += 2, Kp += 2 * kstride) {
+          for (; d + P <= dce; d += 2 * P, Kp += 2 * kstride) {
             const int i = m - d;
             T K0 = __ldg(Kp), K1 = __ldg(Kp + kstride);
             if (LEVELS) {
@@ -425,21 +441,21 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
               K1 = fma(wl, __ldg(Kq + kstride), K1);
               Kq += 2 * kstride;
             }
-            T dM0 = K0 * am * Ns[i], dM1 = K1 * am * Ns[i - 1];
+            T dM0 = K0 * am * Ns[i], dM1 = K1 * am * Ns[i - P];
             if (LIMITED) {
               dM0 *= min_nonneg(Ls[i], ll);
-              dM1 *= min_nonneg(Ls[i - 1], ll);
+              dM1 *= min_nonneg(Ls[i - P], ll);
             }
             stay.add(dM0);
             stay.add(dM1);
             if (!TOP) {
-              const T f0 = tgt.flux(dM0, cds[d], mt), f1 = tgt.flux(dM1, cds[d + 1], mt);
+              const T f0 = tgt.flux(dM0, cds[d], mt), f1 = tgt.flux(dM1, cds[d + P], mt);
               up.add(f0);
               up.add(f1);
             }
           }
         }
-        for (; d <= dce; ++d, Kp += kstride) {
+        for (; d <= dce; d += P, Kp += kstride) {
           const int i = m - d;
           T K = __ldg(Kp);
           if (LEVELS) {
@@ -582,6 +598,16 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
     }
     __syncthreads();
     const int O = ns * ns;
+    // lanes per gain item: points with few items (one or two species) share each item's
+    // pairs among up to 8 lanes, so that they fill more warps and more lanes of each; the
+    // choice depends on the point's shape only, never on the CTA size
+    int lgP = 0;
+    if (t.gain_split > 0) {
+      while ((2 << lgP) <= t.gain_split) ++lgP;
+    } else {
+      while (lgP < 3 && (n - 2) * O * (2 << lgP) <= kSplitLanes) ++lgP;
+    }
+    const int P = 1 << lgP;
 
     int status = 0;
     double emax = 0.0;
@@ -810,10 +836,10 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       //    its cheap end (low k), where a partly filled warp costs least. Warps claim the
       //    top tasks first, then the others costliest first (the cost grows with k).
       {
-        const int n_reg = (n - 2) * O;
+        const int n_reg = ((n - 2) * O) << lgP;  // lanes: P per item, an item's parts adjacent
         const int n_reg_tasks = (n_reg + 31) >> 5;
-        const int pad = n_reg_tasks * 32 - n_reg;
-        const int n_top_tasks = (O + 31) >> 5;
+        const int pad = n_reg_tasks * 32 - n_reg;  // a multiple of P: parts never straddle warps
+        const int n_top_tasks = ((O << lgP) + 31) >> 5;
         const int n_tasks = n_top_tasks + n_reg_tasks;
         for (;;) {
           int q = 0;
@@ -821,22 +847,26 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           q = __shfl_sync(0xffffffffu, q, 0);
           if (q >= n_tasks) break;
           bool on;
-          int ol, k;
+          int ol, k, part;
           if (q < n_top_tasks) {
-            ol = q * 32 + lane;
-            on = ol < O;
-            ol = on ? ol : 0;
+            const int f = q * 32 + lane;
+            on = f < (O << lgP);
+            ol = on ? f >> lgP : 0;
+            part = f & (P - 1);
             k = n - 1;
           } else {
             const int f = (n_reg_tasks - 1 - (q - n_top_tasks)) * 32 + lane - pad;
             on = f >= 0;
-            const int kq = on ? f / O : 0;
-            ol = on ? f - kq * O : 0;
+            const int it = on ? f >> lgP : 0;
+            const int kq = it / O;
+            ol = it - kq * O;
+            part = on ? f & (P - 1) : 0;
             k = kq + 1;
           }
           typename Num<T>::Sum st_, up_;
-#define FSBM_GAIN(LIM, LV, TP) \
-  gain_task<T, LIM, LV, TP>(G, S * S, sm, ori[ol], s_lo, s_hi, k, on, dtT, Bs, t.math, wT, &st_, &up_)
+#define FSBM_GAIN(LIM, LV, TP)                                                                          \
+  gain_task<T, LIM, LV, TP>(G, S * S, sm, ori[ol], s_lo, s_hi, k, on, part, P, dtT, Bs, t.math, wT, &st_, \
+                            &up_)
           const bool top_task = q < n_top_tasks;
           if (LEV && lev) {
             if (limited) {
@@ -852,7 +882,12 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
             }
           }
 #undef FSBM_GAIN
-          if (on && FSBM_OK(t.chk, ol * n + k, O * n)) {
+          // the parts' sums, added pairwise across adjacent lanes (a fixed order); part 0 keeps them
+          for (int off = 1; off < P; off <<= 1) {
+            shfl_add<T>(st_, off);
+            shfl_add<T>(up_, off);
+          }
+          if (on && part == 0 && FSBM_OK(t.chk, ol * n + k, O * n)) {
             sm.stay[ol * n + k] = st_;
             sm.up[ol * n + k] = up_;
           }

@@ -789,7 +789,7 @@ std::string tune_key(const fsbm_coal_ctx* c, double dt, int n_steps, const int32
     std::snprintf(buf, sizeof buf, "|g%d:%d", c->t.g[g].n, c->t.g[g].kappa_max);
     k += buf;
   }
-  std::snprintf(buf, sizeof buf, "|tau%.17g|dt%.17g|n%d|", c->t.tau, dt, n_steps);
+  std::snprintf(buf, sizeof buf, "|tau%.17g|dt%.17g|n%d|P%d|", c->t.tau, dt, n_steps, c->t.gain_split);
   k += buf;
   for (int r = 0; r < n_cls; ++r) k += std::to_string(P > 0 ? (8 * (int64_t)cls_count[r] + P / 2) / P : 0) + ",";
   return k;
@@ -956,6 +956,18 @@ fsbm_status fsbm_coal_set_block(fsbm_coal_ctx* c, int32_t block_dim) {
   c->block_dim = block_dim;
   c->plan_valid = false;
   return ensure_plan(c);
+}
+
+fsbm_status fsbm_coal_set_gain_split(fsbm_coal_ctx* c, int32_t lanes) {
+  if (!c) return FSBM_E_ARG;
+  if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
+    return fail(c, FSBM_E_ARG, "fsbm_coal_set_gain_split: lanes must be 0, 1, 2, 4 or 8");
+  c->t.gain_split = lanes;
+  if (c->gexec) {  // a captured graph holds the old tables by value
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return FSBM_OK;
 }
 
 fsbm_status fsbm_coal_set_timing(fsbm_coal_ctx* c, int32_t enable) {

@@ -93,6 +93,7 @@ struct Tables {
   int64_t rank_cost[kMaxGrids * kMaxSpecies];  // bin pairs per step of a point of each LPT rank
   int mode;                       // 0 pairwise (Jacobi), 1 SWEEP (Bott's in-place order, FP64)
   int levels;                     // 1: kernels at two pressure levels (per-point weight)
+  int gain_split;                 // lanes per gain item (1, 2, 4, 8); 0: chosen per point
   double p1, p2;                  // their pressures, hPa
   double t_min;
   double tau;
