@@ -64,6 +64,31 @@ __device__ __forceinline__ long long warp_max_ll(long long v) {
 // in that range; an integer division by a value known only at run time costs some twenty
 // instructions)
 __device__ __forceinline__ int div_n(int e, unsigned inv_n) { return (int)__umulhi((unsigned)e, inv_n); }
+// x / d for 0 <= x, d < 2^16 through inv = floor(2^32 / d) + 1 (exact there: x (inv d - 2^32)
+// < 2^32); d = 1, whose inverse would not fit, takes inv = 0 and returns x
+__device__ __forceinline__ unsigned div_inv(int d) {
+  return d == 1 ? 0u : (unsigned)(0x100000000ull / (unsigned long long)d + 1);
+}
+__device__ __forceinline__ int div_by(int x, int d, unsigned inv) {
+  return d == 1 ? x : (int)__umulhi((unsigned)x, inv);
+}
+// eight consecutive shared-memory values from a 16-byte aligned address
+__device__ __forceinline__ void lds8(const float* p, float (&v)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void lds8(const double* p, double (&v)[8]) {
+#pragma unroll
+  for (int u = 0; u < 8; u += 2) {
+    const double2 a = *reinterpret_cast<const double2*>(p + u);
+    v[u] = a.x;
+    v[u + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void lds8(const int* p, int (&v)[8]) {
+  const int4 a = *reinterpret_cast<const int4*>(p), b = *reinterpret_cast<const int4*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
 
 // Bott's flux of mass dM deposited in bin k toward bin k + 1 (see fsbm_coal.h).
 __device__ __forceinline__ double bott_flux(double dM, double Mk, double Mk1, double c) {
@@ -215,6 +240,14 @@ template <> struct Acc<float> {
 constexpr int kGainRun = 16;
 constexpr int kLossRun = 32;
 constexpr int kSplitLanes = 128;  // a point's gain items share lanes until they fill 4 warps
+
+// A loss pass cuts its padded column list (a multiple of 8 long) into runs of at most kLossRun
+// columns, at most 2 ns of them (their partial sums fill the two gain arrays), of equal length
+// in blocks of 8 but for the last.
+__device__ __forceinline__ int loss_runs(int cols, int ns) {
+  return max(1, min((cols + kLossRun - 1) / kLossRun, 2 * ns));
+}
+__device__ __forceinline__ int loss_span(int cols, int nch) { return (((cols >> 3) + nch - 1) / nch) << 3; }
 
 // a += (a of lane ^ off), every lane of the warp taking part
 template <typename T>
@@ -608,6 +641,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       while (lgP < 3 && (n - 2) * O * (2 << lgP) <= kSplitLanes) ++lgP;
     }
     const int P = 1 << lgP;
+    // the loss passes' items: (row pair, run of columns), rows 2h and 2h + 1 of one species
+    const int H = (n + 1) >> 1, RP = ns * H;
+    const unsigned inv_H = div_inv(H), inv_RP = div_inv(RP), inv_O = div_inv(O);
 
     int status = 0;
     double emax = 0.0;
@@ -649,15 +685,14 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       // 2. requested loss R and limiter ratios. The active columns (species b, bin j) are
       //    listed once in shared memory as (Kr offset, N), padded with zero entries to a
       //    multiple of 8; Kr is i-fastest, so for a fixed column the rows' entries are
-      //    contiguous and the offset (b, j) is the same for every row. One item per (row,
-      //    run of the list) keeps eight partial sums (eight loads in flight) and parks its sum
-      //    in the gain arrays (free until the gain pass); then one lane per row adds its runs
-      //    in order and forms R and lambda in FP64.
+      //    contiguous and the offset (b, j) is the same for every row. One item per (pair of
+      //    adjacent rows of one species, run of the list): the two rows share each column's
+      //    offset and N, and keep four partial sums each (eight loads in flight); the item parks
+      //    its sums in the gain arrays (free until the gain pass); then one lane per row adds
+      //    its runs in order and forms R and lambda in FP64.
       using Sum = typename Num<T>::Sum;
-      Sum* const part = sm.stay;  // [run][E] partial row sums; the correction's runs reach into
-                                  // sm.up, which follows sm.stay
+      Sum* const part = sm.stay;  // [run][E] partial row sums, reaching into sm.up, which follows
       bool limited = false;
-      const unsigned inv_E = (unsigned)(0x100000000ull / (unsigned long long)E + 1);
       const T* __restrict__ Kr = Sel<T>::Kr(G);
       const T* __restrict__ Krd = lev ? Sel<T>::Kr_d(G) : nullptr;
       int NC = 0;  // active columns, then padded to a multiple of 8
@@ -680,41 +715,54 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       }
       __syncthreads();
       {
-        const int nch = max(1, min((NCp + kLossRun - 1) / kLossRun, ns));
-        const int span = (((NCp + nch - 1) / nch) + 7) & ~7;
-        for (int it = tid; it < nch * E; it += NT) {
-          const int ch = (int)__umulhi((unsigned)it, inv_E), r = it - ch * E;
-          const int a = div_n(r, G.inv_n), i = r - a * n;
-          Acc<T> acc;
-          if (i >= s_lo[a] && i <= s_hi[a] &&
-              (!FSBM_CHECKED_BUILD || (FSBM_OK(t.chk, s_sp[a], S) && FSBM_OK(t.chk, nch * E - 1, S * S * nmax)))) {
+        const int nch = loss_runs(NCp, ns), span = loss_span(NCp, nch);
+        for (int it = tid; it < nch * RP; it += NT) {
+          const int ch = div_by(it, RP, inv_RP), rp = it - ch * RP;
+          const int a = div_by(rp, H, inv_H), i = 2 * (rp - a * H), r = a * n + i;
+          Acc<T> acc0, acc1;
+          if (((i >= s_lo[a] && i <= s_hi[a]) || (i + 1 < n && i + 1 >= s_lo[a] && i + 1 <= s_hi[a])) &&
+              (!FSBM_CHECKED_BUILD || (FSBM_OK(t.chk, s_sp[a], S) && FSBM_OK(t.chk, nch * E - 1, 2 * S * S * nmax)))) {
+            // rows i and i + 1 (which for i = n - 1 reads past the row into the next column, or
+            // into the table's zero padding, and is dropped)
             const T* __restrict__ Krow = Kr + (size_t)s_sp[a] * S * n * n + i;
             const T* __restrict__ Krowd = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
             const int qa = ch * span, qb = min(NCp, qa + span);
             for (int q0 = qa; q0 < qb; q0 += kLossRun) {
               const int q1 = min(qb, q0 + kLossRun);
-              T p[8];
+              T p0[4], p1[4];
 #pragma unroll
-              for (int u = 0; u < 8; ++u) p[u] = T(0);
+              for (int u = 0; u < 4; ++u) p0[u] = p1[u] = T(0);
               for (int q = q0; q < q1; q += 8) {
-                const int4 oa = *reinterpret_cast<const int4*>(sm.loff + q);
-                const int4 ob = *reinterpret_cast<const int4*>(sm.loff + q + 4);
-                const int o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
-                T kk[8];
+                int o[8];
+                T nj[8], k0[8], k1[8];
+                lds8(sm.loff + q, o);
+                lds8(sm.lN + q, nj);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) kk[u] = __ldg(Krow + o[u]);
+                for (int u = 0; u < 8; ++u) {
+                  k0[u] = __ldg(Krow + o[u]);
+                  k1[u] = __ldg(Krow + o[u] + 1);
+                }
                 if (lev) {
 #pragma unroll
-                  for (int u = 0; u < 8; ++u) kk[u] = fma(wT, __ldg(Krowd + o[u]), kk[u]);
+                  for (int u = 0; u < 8; ++u) {
+                    k0[u] = fma(wT, __ldg(Krowd + o[u]), k0[u]);
+                    k1[u] = fma(wT, __ldg(Krowd + o[u] + 1), k1[u]);
+                  }
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) p[u] = fma(kk[u], sm.lN[q + u], p[u]);
+                for (int u = 0; u < 8; ++u) {
+                  p0[u & 3] = fma(k0[u], nj[u], p0[u & 3]);
+                  p1[u & 3] = fma(k1[u], nj[u], p1[u & 3]);
+                }
               }
-              acc.add(((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
-              acc.flush();
+              acc0.add((p0[0] + p0[1]) + (p0[2] + p0[3]));
+              acc0.flush();
+              acc1.add((p1[0] + p1[1]) + (p1[2] + p1[3]));
+              acc1.flush();
             }
           }
-          part[it] = acc.sum();
+          part[ch * E + r] = acc0.sum();
+          if (i + 1 < n) part[ch * E + r + 1] = acc1.sum();
         }
         __syncthreads();
         bool fired = false;
@@ -743,9 +791,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       //      = lam_i R_i + dt M_i sum_{j limited} K N_j (min(lam_i, lam_j) - lam_i),
       //    where lam_i R_i = M_i when lam_i < 1 and every term with lam_j >= lam_i is 0. The
       //    limited rows are listed in row order as columns (Kr offset, N, lambda), padded with
-      //    zero entries to a multiple of 8; one item per (row, run of the list), at most 2 ns
-      //    runs per row so that the items fit in the gain arrays; then one lane per row adds
-      //    its runs in order.
+      //    zero entries to a multiple of 8; one item per (row pair, run of the list) as in the
+      //    requested loss; then one lane per row adds its runs in order.
       if (limited) {
         if (warp == 0) {
           int cnt = 0;
@@ -775,44 +822,55 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           }
         }
         __syncthreads();
-        const int nch = max(1, min((Lp + kLossRun - 1) / kLossRun, 2 * ns));
-        const int span = (((Lp + nch - 1) / nch) + 7) & ~7;
-        for (int it = tid; it < nch * E; it += NT) {
-          const int ch = (int)__umulhi((unsigned)it, inv_E), r = it - ch * E;
-          const int a = div_n(r, G.inv_n), i = r - a * n;
-          Acc<T> acc;
-          if (i >= s_lo[a] && i <= s_hi[a] &&
+        const int nch = loss_runs(Lp, ns), span = loss_span(Lp, nch);
+        for (int it = tid; it < nch * RP; it += NT) {
+          const int ch = div_by(it, RP, inv_RP), rp = it - ch * RP;
+          const int a = div_by(rp, H, inv_H), i = 2 * (rp - a * H), r = a * n + i;
+          Acc<T> acc0, acc1;
+          if (((i >= s_lo[a] && i <= s_hi[a]) || (i + 1 < n && i + 1 >= s_lo[a] && i + 1 <= s_hi[a])) &&
               (!FSBM_CHECKED_BUILD || (FSBM_OK(t.chk, s_sp[a], S) && FSBM_OK(t.chk, L, E + 1) &&
                                        FSBM_OK(t.chk, nch * E - 1, 2 * S * S * nmax)))) {
-            const T li = sm.lam[r];
+            const T li0 = sm.lam[r], li1 = i + 1 < n ? sm.lam[r + 1] : T(1);
             const T* __restrict__ Krow = Kr + (size_t)s_sp[a] * S * n * n + i;
             const T* __restrict__ Krowd = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
             const int qa = ch * span, qb = min(Lp, qa + span);
             for (int q0 = qa; q0 < qb; q0 += kLossRun) {
               const int q1 = min(qb, q0 + kLossRun);
-              T p[8];
+              T p0[4], p1[4];
 #pragma unroll
-              for (int u = 0; u < 8; ++u) p[u] = T(0);
+              for (int u = 0; u < 4; ++u) p0[u] = p1[u] = T(0);
               for (int q = q0; q < q1; q += 8) {
-                const int4 oa = *reinterpret_cast<const int4*>(sm.loff + q);
-                const int4 ob = *reinterpret_cast<const int4*>(sm.loff + q + 4);
-                const int o[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
-                T kk[8];
+                int o[8];
+                T nj[8], lj[8], k0[8], k1[8];
+                lds8(sm.loff + q, o);
+                lds8(sm.lN + q, nj);
+                lds8(sm.llam + q, lj);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) kk[u] = __ldg(Krow + o[u]);
+                for (int u = 0; u < 8; ++u) {
+                  k0[u] = __ldg(Krow + o[u]);
+                  k1[u] = __ldg(Krow + o[u] + 1);
+                }
                 if (lev) {
 #pragma unroll
-                  for (int u = 0; u < 8; ++u) kk[u] = fma(wT, __ldg(Krowd + o[u]), kk[u]);
+                  for (int u = 0; u < 8; ++u) {
+                    k0[u] = fma(wT, __ldg(Krowd + o[u]), k0[u]);
+                    k1[u] = fma(wT, __ldg(Krowd + o[u] + 1), k1[u]);
+                  }
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                  p[u] = fma((min_nonneg(li, sm.llam[q + u]) - li) * kk[u], sm.lN[q + u], p[u]);
+                for (int u = 0; u < 8; ++u) {
+                  p0[u & 3] = fma((min_nonneg(li0, lj[u]) - li0) * k0[u], nj[u], p0[u & 3]);
+                  p1[u & 3] = fma((min_nonneg(li1, lj[u]) - li1) * k1[u], nj[u], p1[u & 3]);
+                }
               }
-              acc.add(((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
-              acc.flush();
+              acc0.add((p0[0] + p0[1]) + (p0[2] + p0[3]));
+              acc0.flush();
+              acc1.add((p1[0] + p1[1]) + (p1[2] + p1[3]));
+              acc1.flush();
             }
           }
-          part[it] = acc.sum();
+          part[ch * E + r] = acc0.sum();
+          if (i + 1 < n) part[ch * E + r + 1] = acc1.sum();
         }
         __syncthreads();
         for (int r = tid; r < E; r += NT) {
@@ -858,7 +916,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
             const int f = (n_reg_tasks - 1 - (q - n_top_tasks)) * 32 + lane - pad;
             on = f >= 0;
             const int it = on ? f >> lgP : 0;
-            const int kq = it / O;
+            const int kq = div_by(it, O, inv_O);
             ol = it - kq * O;
             part = on ? f & (P - 1) : 0;
             k = kq + 1;

@@ -421,7 +421,7 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
     // the two layouts of one grid's kernel tables
     auto layouts = [&](const double* Kt, std::vector<double>& Kd, std::vector<double>& Kr) {
       Kd.assign((size_t)S2 * nn, 0.0);
-      Kr.assign((size_t)S2 * nn, 0.0);
+      Kr.assign((size_t)S2 * nn + kKrPad, 0.0);
       for (int s = 0; s < S; ++s)
         for (int l = 0; l < S; ++l) {
           double* kr = Kr.data() + (size_t)(s * S + l) * nn;

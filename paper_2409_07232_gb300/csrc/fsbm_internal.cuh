@@ -135,6 +135,9 @@ struct Scratch {
   int64_t n_blocks;
 };
 
+// zero entries after every Kr table: a loss item's second row reads one entry past the
+// last column's first row
+constexpr int kKrPad = 8;
 constexpr int kMaxShards = 1024;
 
 // Equal-cost contiguous shards of a cost-ordered list. Grid points are independent (Sec. VI-A),
