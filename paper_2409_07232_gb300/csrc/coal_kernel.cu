@@ -647,6 +647,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
 
     int status = 0;
     double emax = 0.0;
+    const double inv_B0 = 1.0 / B0;  // mass errors are relative to the budget
     for (int step = 0; step < n_steps; ++step) {
       // 1. budget and active ranges. The budget of every step is the point's mass B0: each
       //    step ends rescaled to it (the start-of-step total equals B0 to rounding).
@@ -982,12 +983,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
         pre = warp_sum(pre);
         post = warp_sum(post);
         if (lane == 0) {
-          red[0] = fabs(pre - Bs) / Bs;
+          emax = fmax(emax, fabs(pre - Bs) * inv_B0);  // thread 0 keeps the running maximum
           red[1] = Bs / post;
         }
       }
       __syncthreads();
-      emax = fmax(emax, red[0]);
       const double scale = red[1];
       for (int e = tid; e < E; e += NT) sm.M[e] = sm.M[e] * scale;
       __syncthreads();
