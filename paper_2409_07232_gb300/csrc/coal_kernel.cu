@@ -118,6 +118,11 @@ __device__ __forceinline__ double bott_flux(double dM, double Mk, double Mk1, do
 //       z = 0: sinh(y)/y = 1 + y^2/6 + y^4/120 + y^6/5040, next term below 1.1e-8), and
 //     (1 - e^{-z}) / x1 = (1 - (e^{-z/2})^2) / x1        otherwise;
 //   both are formed and one is selected, so the lanes of a warp never diverge here.
+// The code works in base-2 units, which saves the multiply by ln 2: l = log2(rho) clamped to
+// [log2 1e-60, 80 / ln 2] (x1 = l ln 2) and zl = c l (z = zl ln 2); with the factor ln 2 moved
+// into the constants, F = dM A' r' where A' = e^{x1/2} / ln 2 = 2^{l/2 - log2 ln 2} and r' =
+// ln 2 (1 - e^{-z}) / x1 is c w ln 2 sinh(z/2)/(z/2) (the series in zl^2, each coefficient
+// times the matching power of ln 2) for |zl| <= 1 / ln 2, or (1 - w^2) / l, w = 2^{-zl/2}.
 // Five SFU operations per pair: the two reciprocals, log2, e^{x1/2} and e^{-z/2}. They flush
 // subnormal inputs and results to zero (one SFU instruction each, no subnormal fix-up): a ratio
 // rho below FP32's normal range then reads as 0 (x1 = ln 1e-60) and a sum g below it as an
@@ -138,22 +143,29 @@ __device__ __forceinline__ float sfu_ex2(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-constexpr float kLn2f = 0.693147182f;
-constexpr float kHalfLog2ef = 0.721347520f;  // log2(e) / 2
+constexpr double kLn2d = 0.69314718055994531;
+constexpr float kLog2BottEps = (float)(-138.15510557964274 / kLn2d);  // log2(1e-60)
+constexpr float kLog2Cap = (float)(80.0 / kLn2d);                     // 80 / ln 2
+constexpr float kLog2InvLn2 = 0.52876637294f;                         // -log2(ln 2)
+constexpr float kInvLn2f = (float)(1.0 / kLn2d);
+constexpr float kS0 = (float)kLn2d;  // ln 2 (1 + u / 24 + u^2 / 1920 + u^3 / 322560), u = z^2
+constexpr float kS1 = (float)(kLn2d * kLn2d * kLn2d / 24.0);
+constexpr float kS2 = (float)(kLn2d * kLn2d * kLn2d * kLn2d * kLn2d / 1920.0);
+constexpr float kS3 = (float)(kLn2d * kLn2d * kLn2d * kLn2d * kLn2d * kLn2d * kLn2d / 322560.0);
 __device__ __forceinline__ float bott_flux_f32(float dM, float Mk, float Mk1, float c) {
   const float g = Mk + dM;
   const float rho = Mk1 * sfu_rcp(g);
-  const float x1 = fminf(fmaxf(sfu_lg2(rho) * kLn2f, kLnBottEps), 80.f);
-  const float z = c * x1;
-  const float A = sfu_ex2(x1 * kHalfLog2ef);    // e^{x1/2}
-  const float w = sfu_ex2(z * -kHalfLog2ef);    // e^{-z/2}
-  const float z2 = z * z;
-  float P = fmaf(z2, 1.f / 322560.f, 1.f / 1920.f);
-  P = fmaf(z2, P, 1.f / 24.f);
-  P = fmaf(z2, P, 1.f);
+  const float l = fminf(fmaxf(sfu_lg2(rho), kLog2BottEps), kLog2Cap);  // x1 / ln 2
+  const float zl = c * l;                                               // z / ln 2
+  const float A = sfu_ex2(fmaf(l, 0.5f, kLog2InvLn2));                  // e^{x1/2} / ln 2
+  const float w = sfu_ex2(zl * -0.5f);                                  // e^{-z/2}
+  const float u = zl * zl;                                              // z^2 / ln^2 2
+  float P = fmaf(u, kS3, kS2);
+  P = fmaf(u, P, kS1);
+  P = fmaf(u, P, kS0);
   const float near0 = c * w * P;
-  const float far = fmaf(-w, w, 1.f) * sfu_rcp(x1);  // an overflowing e^{-z} gives +inf: F = dM
-  const float ratio = fabsf(z) <= 1.f ? near0 : far;
+  const float far = fmaf(-w, w, 1.f) * sfu_rcp(l);  // an overflowing e^{-z} gives +inf: F = dM
+  const float ratio = fabsf(zl) <= kInvLn2f ? near0 : far;
   return fminf(dM * (A * ratio), dM);  // A * ratio first: dM * A alone can underflow; fminf
                                        // keeps dM where dM * inf gave inf or 0 * inf NaN
 }
@@ -237,7 +249,11 @@ template <> struct Acc<float> {
     return t;
   }
 };
-constexpr int kGainRun = 16;
+// pairs a gain lane adds in T before folding the run into its total: FP32 runs of 32 (one run
+// per item on the 33-bin grid); FP64 adds every term in FP64, so one run per group
+template <typename T> struct GainRun;
+template <> struct GainRun<float> { static constexpr int value = 32; };
+template <> struct GainRun<double> { static constexpr int value = 1 << 20; };
 constexpr int kLossRun = 32;
 constexpr int kSplitLanes = 128;  // a point's gain items share lanes until they fill 4 warps
 
@@ -457,9 +473,9 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
       const ptrdiff_t e0 = (ptrdiff_t)((d0 + p) * n + m) * S2;
       const T* __restrict__ Kp = Kd + e0;
       const T* __restrict__ Kq = LEVELS ? Kdd + e0 : nullptr;
-      // runs of up to kGainRun pairs, each folded into the running totals after it
-      for (int dc = d0 + p; dc <= d1; dc += kGainRun * P) {
-        const int dce = min(d1, dc + (kGainRun - 1) * P);
+      // runs of up to GainRun pairs, each folded into the running totals after it
+      for (int dc = d0 + p; dc <= d1; dc += GainRun<T>::value * P) {
+        const int dce = min(d1, dc + (GainRun<T>::value - 1) * P);
         int d = dc;
         if (sizeof(T) == sizeof(float)) {
           // FP32: two pairs per iteration, so that two flux chains (each a string of dependent

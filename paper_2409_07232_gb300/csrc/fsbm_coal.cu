@@ -801,39 +801,42 @@ fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
   if (st != FSBM_OK) return st;
   c->tune_cache_hit = 0;
   if (n_points == 0) return FSBM_OK;
-  // The first 2^16 points (all if fewer) give the batch's class mix; the timed sample is a
-  // prefix of them holding about kTuneWork pair updates at the caller's dt and up to 4 of its
-  // steps (at least 2432 points, several per resident CTA, so that the last points' tail
-  // weighs about as much as in a real call), which keeps a tuning call near 0.1 s per
+  // The whole batch is classified and ordered, as a step would (on a copy of the spectra and
+  // scratch outputs, so the caller's arrays are left alone), which gives its class mix. The
+  // timed sample is an even stride through the ordered active list holding about kTuneWork
+  // pair updates at the caller's dt and up to 4 of its steps (at least 2432 points, several per
+  // resident CTA, so that the last points' tail weighs about as much as in a real call): every
+  // class in its share and order, wherever in the batch its points lie, and about 0.1 s per
   // candidate for any grid.
-  const int64_t P = std::min<int64_t>(n_points, 1 << 16);
   int64_t off[2];
   CU(c, cudaMemcpyAsync(&off[0], s->offset, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-  CU(c, cudaMemcpyAsync(&off[1], s->offset + P, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(c, cudaMemcpyAsync(&off[1], s->offset + n_points, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   CU(c, cudaStreamSynchronize(c->stream));
   const size_t esz = c->precision == FSBM_FP64 ? sizeof(double) : sizeof(float);
   const size_t bytes = (size_t)(off[1] - off[0]) * esz;
+  const size_t spec_b = (bytes + 15) & ~size_t(15);
+  const size_t outb = ((sizeof(double) * 2 + sizeof(int32_t)) * (size_t)n_points + 15) & ~size_t(15);
   char* tmp = nullptr;
-  const size_t outb = (sizeof(double) * 2 + sizeof(int32_t)) * (size_t)P;
-  CU(c, cudaMalloc(&tmp, bytes + outb + 64));
-  char* src = static_cast<char*>(s->spectra) + (size_t)off[0] * esz;
-  PointsDev p = to_dev(s, P);
+  CU(c, cudaMalloc(&tmp, spec_b + outb + sizeof(int32_t) * (size_t)n_points + 64));
+  const char* src = static_cast<const char*>(s->spectra) + (size_t)off[0] * esz;
+  PointsDev p = to_dev(s, n_points);
   p.spectra = tmp - (size_t)off[0] * esz;
-  p.mass_budget = reinterpret_cast<double*>(tmp + ((bytes + 15) & ~size_t(15)));
-  p.mass_error = p.mass_budget + P;
-  p.status = reinterpret_cast<int32_t*>(p.mass_error + P);
-  st = ensure_scratch(c, std::max<int64_t>(n_points, P));
+  p.mass_budget = reinterpret_cast<double*>(tmp + spec_b);
+  p.mass_error = p.mass_budget + n_points;
+  p.status = reinterpret_cast<int32_t*>(p.mass_error + n_points);
+  int32_t* sample_list = reinterpret_cast<int32_t*>(tmp + spec_b + outb);
+  st = ensure_scratch(c, n_points);
   if (st != FSBM_OK) {
     cudaFree(tmp);
     return st;
   }
-  const int64_t nblk = (P + kCompactThreads - 1) / kCompactThreads;
-  c->scratch.n_blocks = nblk;
-  // the sample's class mix: first positions of the classes in the ordered list (the scanned
-  // counts' first block of every class) and the active count
+  const int64_t nblk = c->scratch.n_blocks;
+  // the class mix: first positions of the classes in the ordered list (the scanned counts'
+  // first block of every class) and the active count
   const int n_cls = c->G * c->S;
   int32_t first[kNumBuckets + 1] = {};
-  cudaError_t ce = launch_compact(c->t, p, P, c->scratch, c->stream);
+  cudaError_t ce = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (ce == cudaSuccess) ce = launch_compact(c->t, p, n_points, c->scratch, c->stream);
   for (int r = 0; r < n_cls && ce == cudaSuccess; ++r)
     ce = cudaMemcpyAsync(&first[r], c->scratch.block_counts + (int64_t)r * nblk, sizeof(int32_t),
                          cudaMemcpyDeviceToHost, c->stream);
@@ -844,26 +847,18 @@ fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
     cudaFree(tmp);
     return cuda_fail(c, ce, who);
   }
+  const int64_t n_act = first[n_cls];
   int32_t cls_count[kNumBuckets] = {};
-  double work = 0.0, act = 0.0;
+  double work = 0.0;
   for (int r = 0; r < n_cls; ++r) {
     cls_count[r] = first[r + 1] - first[r];
     work += (double)cls_count[r] * (double)c->t.rank_cost[r];
-    act += cls_count[r];
   }
-  const std::string key = tune_key(c, dt, n_steps, cls_count, n_cls, P);
-  const int tune_steps = std::min(n_steps, 4);
-  const double kTuneWork = c->precision == FSBM_FP64 ? 1.5e9 : 3e10;  // pair updates per run
-  const double per_point = work / (double)P;  // pair updates per step per sample point (clear ones cost 0)
-  const int64_t Pt = std::max<int64_t>(
-      std::min<int64_t>(P, 2432), std::min<int64_t>(P, (int64_t)(kTuneWork / std::max(per_point * tune_steps, 1.0))));
-  size_t tbytes = bytes;
-  if (Pt < P) {
-    int64_t offt = 0;
-    CU(c, cudaMemcpyAsync(&offt, s->offset + Pt, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-    CU(c, cudaStreamSynchronize(c->stream));
-    tbytes = (size_t)(offt - off[0]) * esz;
+  if (n_act == 0) {  // nothing would be stepped: no candidate to time
+    cudaFree(tmp);
+    return FSBM_OK;
   }
+  const std::string key = tune_key(c, dt, n_steps, cls_count, n_cls, n_act);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -875,9 +870,28 @@ fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
       return ensure_plan(c);
     }
   }
-  PointsDev pt = p;  // the timed sample: the first Pt points of the copy
-  pt.n_points = Pt;
-  c->scratch.n_blocks = (Pt + kCompactThreads - 1) / kCompactThreads;
+  const int tune_steps = std::min(n_steps, 4);
+  const double kTuneWork = c->precision == FSBM_FP64 ? 1.5e9 : 3e10;  // pair updates per run
+  const double per_point = work / (double)n_act;                      // pair updates per step
+  const int64_t Pt = std::max<int64_t>(std::min<int64_t>(n_act, 2432),
+                                       std::min<int64_t>(n_act, (int64_t)(kTuneWork / std::max(per_point * tune_steps, 1.0))));
+  {
+    std::vector<int32_t> full((size_t)n_act), samp((size_t)Pt);
+    ce = cudaMemcpyAsync(full.data(), c->scratch.active_list, sizeof(int32_t) * (size_t)n_act,
+                         cudaMemcpyDeviceToHost, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    for (int64_t q = 0; q < Pt && ce == cudaSuccess; ++q) samp[(size_t)q] = full[(size_t)(q * n_act / Pt)];
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(sample_list, samp.data(), sizeof(int32_t) * (size_t)Pt, cudaMemcpyHostToDevice, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(c, ce, who);
+    }
+  }
+  Scratch ts = c->scratch;  // the sample's list; the queue counters are reset before every run
+  ts.active_list = sample_list;
+  const int32_t cnt[4] = {(int32_t)Pt, 0, (int32_t)Pt, 0};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -891,10 +905,10 @@ fsbm_status autotune_at(fsbm_coal_ctx* c, const fsbm_coal_state* s, int64_t n_po
     if (coal_plan(c->t, c->precision, b, c->n_sms, &plan) != cudaSuccess) continue;
     float ms_tot = 0.f;
     for (int rep = 0; rep < 2; ++rep) {
-      cudaMemcpyAsync(tmp, src, tbytes, cudaMemcpyDeviceToDevice, c->stream);
-      launch_compact(c->t, pt, Pt, c->scratch, c->stream);
+      cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+      cudaMemcpyAsync(c->scratch.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, c->stream);
       cudaEventRecord(e0, c->stream);
-      launch_coal(c->t, c->precision, pt, c->scratch, dt, tune_steps, plan, c->stream);
+      launch_coal(c->t, c->precision, p, ts, dt, tune_steps, plan, c->stream);
       cudaEventRecord(e1, c->stream);
       cudaEventSynchronize(e1);
       float ms = 0.f;
