@@ -278,6 +278,12 @@ __device__ __forceinline__ void shfl_add<float>(FF& a, int off) {
   ff_add(a, b);
 }
 
+// N and lambda of one bin side by side: the gain pass reads both of a pair's smaller bin at once
+template <typename T>
+struct __align__(2 * sizeof(T)) NLPair {
+  T n, l;
+};
+
 // Shared-memory carve-up for nmax bins and S species (T = pair-arithmetic type).
 template <typename T>
 struct Smem {
@@ -289,6 +295,7 @@ struct Smem {
   T* Mt;          // [S][nmax] state in T (aliases M when T = double)
   T* N;           // [S][nmax]
   T* lam;         // [S][nmax]
+  NLPair<T>* NL;  // [S][nmax] (N, lambda) of every bin, once lambda is known
   T* xs;          // [nmax]
   T* cd;          // [nmax] Courant number per bin distance
   T* llam;        // [S*nmax + 8] ratios of the listed columns (limited rows), padded to 8
@@ -301,7 +308,8 @@ struct Smem {
     const size_t e = (size_t)S * nmax, l = e + 8;
     size_t b = 2 * up16(sizeof(double) * e) + 2 * up16(sizeof(Sum) * S * e);
     if (sizeof(T) != sizeof(double)) b += up16(sizeof(T) * e);
-    b += 2 * up16(sizeof(T) * e) + 2 * up16(sizeof(T) * nmax) + 2 * up16(sizeof(T) * l) + 2 * up16(sizeof(int) * l);
+    b += 2 * up16(sizeof(T) * e) + up16(sizeof(NLPair<T>) * e) + 2 * up16(sizeof(T) * nmax) + 2 * up16(sizeof(T) * l) +
+         2 * up16(sizeof(int) * l);
     return b;
   }
   __device__ void carve(unsigned char* base, int nmax, int S) {
@@ -319,6 +327,7 @@ struct Smem {
     Mt = sizeof(T) != sizeof(double) ? reinterpret_cast<T*>(take(sizeof(T) * e)) : reinterpret_cast<T*>(M);
     N = reinterpret_cast<T*>(take(sizeof(T) * e));
     lam = reinterpret_cast<T*>(take(sizeof(T) * e));
+    NL = reinterpret_cast<NLPair<T>*>(take(sizeof(NLPair<T>) * e));
     xs = reinterpret_cast<T*>(take(sizeof(T) * nmax));
     cd = reinterpret_cast<T*>(take(sizeof(T) * nmax));
     llam = reinterpret_cast<T*>(take(sizeof(T) * l));
@@ -447,9 +456,8 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
   Acc<T> stay, up;
   const T* __restrict__ Kd = Sel<T>::Kd(G) + o.table;
   const T* __restrict__ Kdd = LEVELS ? Sel<T>::Kd_d(G) + o.table : nullptr;
-  const T* __restrict__ Ns = sm.N + o.s * n;
+  const NLPair<T>* __restrict__ NLs = sm.NL + o.s * n;
   const T* __restrict__ Ml = sm.Mt + o.l * n;
-  const T* __restrict__ Ls = sm.lam + o.s * n;
   const T* __restrict__ Ll = sm.lam + o.l * n;
   const T* __restrict__ cds = sm.cd;
   const int lo_s = lo[o.s], hi_s = hi[o.s], lo_l = lo[o.l], hi_l = hi[o.l];
@@ -458,6 +466,8 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
   TargetOf<T> tgt;
   if (!TOP) tgt.init(on ? sm.Mt[o.c * n + k] : T(0), on ? sm.Mt[o.c * n + k + 1] : T(0), B, mt);
   const int kstride = n * S2 * P;  // table step from one of this part's distances to the next
+  const int lgP = __ffs(P) - 1;
+  int run = 0;  // FP32: pairs added to the open run since it was last folded into the totals
   for (int kap = 0; kap <= G.kappa_max; ++kap) {
     const int dlo = max(G.d_lo[kap], (int)o.dmin), dhi = G.d_hi[kap];
     const int m0 = max(TOP ? n - 1 - kap : k - kap, lo_l);
@@ -473,9 +483,19 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
       const ptrdiff_t e0 = (ptrdiff_t)((d0 + p) * n + m) * S2;
       const T* __restrict__ Kp = Kd + e0;
       const T* __restrict__ Kq = LEVELS ? Kdd + e0 : nullptr;
-      // runs of up to GainRun pairs, each folded into the running totals after it
+      // chunks of up to GainRun pairs; the open run is folded into the totals before a chunk
+      // that would take it past GainRun pairs (and at the end of the item)
       for (int dc = d0 + p; dc <= d1; dc += GainRun<T>::value * P) {
         const int dce = min(d1, dc + (GainRun<T>::value - 1) * P);
+        if (sizeof(T) == sizeof(float)) {
+          const int len = ((dce - dc) >> lgP) + 1;
+          if (run + len > GainRun<T>::value) {
+            stay.flush();
+            up.flush();
+            run = 0;
+          }
+          run += len;
+        }
         int d = dc;
         if (sizeof(T) == sizeof(float)) {
           // FP32: two pairs per iteration, so that two flux chains (each a string of dependent
@@ -490,10 +510,11 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
               K1 = fma(wl, __ldg(Kq + kstride), K1);
               Kq += 2 * kstride;
             }
-            T dM0 = K0 * am * Ns[i], dM1 = K1 * am * Ns[i - P];
+            const NLPair<T> a0 = NLs[i], a1 = NLs[i - P];
+            T dM0 = K0 * am * a0.n, dM1 = K1 * am * a1.n;
             if (LIMITED) {
-              dM0 *= min_nonneg(Ls[i], ll);
-              dM1 *= min_nonneg(Ls[i - P], ll);
+              dM0 *= min_nonneg(a0.l, ll);
+              dM1 *= min_nonneg(a1.l, ll);
             }
             stay.add(dM0);
             stay.add(dM1);
@@ -511,18 +532,18 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
             K = fma(wl, __ldg(Kq), K);
             Kq += kstride;
           }
-          T dM = K * am * Ns[i];
-          if (LIMITED) dM *= min_nonneg(Ls[i], ll);
+          const NLPair<T> a = NLs[i];
+          T dM = K * am * a.n;
+          if (LIMITED) dM *= min_nonneg(a.l, ll);
           stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
           if (!TOP) {    // none out of the top bin
             const T c = cds[d];
-            // c = 0 (the pair lands exactly on bin k): F = 0. The FP32 flux gives 0 there by
-            // itself; the FP64 one is skipped (a whole group of d = 0 pairs at once)
-            if (sizeof(T) == sizeof(float) || !is_zero(c)) up.add(tgt.flux(dM, c, mt));
+            // c = 0 (the pair lands exactly on bin k): F = 0, skipped. Every d = 0 pair (two
+            // equal bins: x_m + x_m = x_{m+s} exactly) forms a group of its own and comes
+            // through here, so a warp skips it as a whole; the FP32 flux would give 0 too
+            if (!is_zero(c)) up.add(tgt.flux(dM, c, mt));
           }
         }
-        stay.flush();
-        up.flush();
       }
     }
   }
@@ -798,6 +819,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           }
           sm.loss[r] = R;
           sm.lam[r] = (T)lamd;
+          sm.NL[r] = NLPair<T>{sm.N[r], (T)lamd};
         }
         if (tid == 0) s_task = 0;
         limited = __syncthreads_or(fired);
