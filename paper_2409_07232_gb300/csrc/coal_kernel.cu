@@ -293,9 +293,9 @@ struct Smem {
   Sum* stay;      // [S*S][nmax] per-orientation partial gains of bin k
   Sum* up;        // [S*S][nmax] per-orientation fluxes from bin k to k+1
   T* Mt;          // [S][nmax] state in T (aliases M when T = double)
-  T* N;           // [S][nmax]
-  T* lam;         // [S][nmax]
-  NLPair<T>* NL;  // [S][nmax] (N, lambda) of every bin, once lambda is known
+  NLPair<T>* NL;  // [S][nmax] (N, lambda) of every bin: N from step 1, lambda from step 2
+  T* nlam;        // FP64 form: [S][nmax] N lambda of every bin (else NULL)
+  T* lNl;         // FP64 form: [S*nmax + 8] N lambda of the listed columns, padded to 8 (else NULL)
   T* xs;          // [nmax]
   T* cd;          // [nmax] Courant number per bin distance
   T* llam;        // [S*nmax + 8] ratios of the listed columns (limited rows), padded to 8
@@ -308,8 +308,8 @@ struct Smem {
     const size_t e = (size_t)S * nmax, l = e + 8;
     size_t b = 2 * up16(sizeof(double) * e) + 2 * up16(sizeof(Sum) * S * e);
     if (sizeof(T) != sizeof(double)) b += up16(sizeof(T) * e);
-    b += 2 * up16(sizeof(T) * e) + up16(sizeof(NLPair<T>) * e) + 2 * up16(sizeof(T) * nmax) + 2 * up16(sizeof(T) * l) +
-         2 * up16(sizeof(int) * l);
+    b += up16(sizeof(NLPair<T>) * e) + 2 * up16(sizeof(T) * nmax) + 2 * up16(sizeof(T) * l) + 2 * up16(sizeof(int) * l);
+    if (sizeof(T) == sizeof(double)) b += up16(sizeof(T) * e) + up16(sizeof(T) * l);
     return b;
   }
   __device__ void carve(unsigned char* base, int nmax, int S) {
@@ -325,8 +325,6 @@ struct Smem {
     stay = reinterpret_cast<Sum*>(take(sizeof(Sum) * S * e));
     up = reinterpret_cast<Sum*>(take(sizeof(Sum) * S * e));
     Mt = sizeof(T) != sizeof(double) ? reinterpret_cast<T*>(take(sizeof(T) * e)) : reinterpret_cast<T*>(M);
-    N = reinterpret_cast<T*>(take(sizeof(T) * e));
-    lam = reinterpret_cast<T*>(take(sizeof(T) * e));
     NL = reinterpret_cast<NLPair<T>*>(take(sizeof(NLPair<T>) * e));
     xs = reinterpret_cast<T*>(take(sizeof(T) * nmax));
     cd = reinterpret_cast<T*>(take(sizeof(T) * nmax));
@@ -334,6 +332,8 @@ struct Smem {
     lN = reinterpret_cast<T*>(take(sizeof(T) * l));
     lim = reinterpret_cast<int*>(take(sizeof(int) * l));
     loff = reinterpret_cast<int*>(take(sizeof(int) * l));
+    nlam = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(take(sizeof(T) * e)) : nullptr;
+    lNl = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(take(sizeof(T) * l)) : nullptr;
   }
 };
 
@@ -362,6 +362,11 @@ __device__ __forceinline__ double min_nonneg(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b) ? a : b;
 }
 __device__ __forceinline__ float min_nonneg(float a, float b) { return fminf(a, b); }
+// a < b for non-negative doubles, on the integer pipes
+__device__ __forceinline__ bool lt_nonneg(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ bool lt_nonneg(float a, float b) { return a < b; }
 // Bott's flux with target-bin constants hoisted out of the pair loop:
 //  * bin k+1 holds at least 1e-43 of the largest content bin k can reach (Mk + 2B): then
 //    1e-60 g is below half an ulp of M_{k+1}, M_{k+1} + 1e-60 g rounds to M_{k+1} exactly, and
@@ -457,8 +462,9 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
   const T* __restrict__ Kd = Sel<T>::Kd(G) + o.table;
   const T* __restrict__ Kdd = LEVELS ? Sel<T>::Kd_d(G) + o.table : nullptr;
   const NLPair<T>* __restrict__ NLs = sm.NL + o.s * n;
+  const T* __restrict__ NLm = sizeof(T) == sizeof(double) ? sm.nlam + o.s * n : nullptr;
   const T* __restrict__ Ml = sm.Mt + o.l * n;
-  const T* __restrict__ Ll = sm.lam + o.l * n;
+  const NLPair<T>* __restrict__ NLl = sm.NL + o.l * n;
   const T* __restrict__ cds = sm.cd;
   const int lo_s = lo[o.s], hi_s = hi[o.s], lo_l = lo[o.l], hi_l = hi[o.l];
   on = on && k >= 1 && k < n;
@@ -479,7 +485,8 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
             FSBM_OK(G.chk, m - d0, n) && FSBM_OK(G.chk, ((ptrdiff_t)d1 * n + m) * S2 + o.table, (ptrdiff_t)S2 * n * n)))
         continue;
       const T am = Ml[m] * dt;
-      const T ll = LIMITED ? Ll[m] : T(1);
+      const T ll = LIMITED ? NLl[m].l : T(1);
+      const T amll = am * ll;  // FP64 limited pairs whose ratio min is the larger bin's
       const ptrdiff_t e0 = (ptrdiff_t)((d0 + p) * n + m) * S2;
       const T* __restrict__ Kp = Kd + e0;
       const T* __restrict__ Kq = LEVELS ? Kdd + e0 : nullptr;
@@ -533,8 +540,16 @@ __device__ __forceinline__ void gain_task(const GridDev& G, int S2, const Smem<T
             Kq += kstride;
           }
           const NLPair<T> a = NLs[i];
-          T dM = K * am * a.n;
-          if (LIMITED) dM *= min_nonneg(a.l, ll);
+          T dM;
+          if (LIMITED && sizeof(T) == sizeof(double)) {
+            // min(l_i, l_m) N_i (M_m dt) as two multiplies: (N_i l_i)(M_m dt) when l_i <= l_m,
+            // else N_i (M_m dt l_m), chosen on the bit patterns
+            const bool own = !lt_nonneg(ll, a.l);
+            dM = K * (own ? am : amll) * (own ? NLm[i] : a.n);
+          } else {
+            dM = K * am * a.n;
+            if (LIMITED) dM *= min_nonneg(a.l, ll);
+          }
           stay.add(dM);  // the pair's whole mass; the flux is taken back out at the end
           if (!TOP) {    // none out of the top bin
             const T c = cds[d];
@@ -715,7 +730,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
       for (int e = tid; e < E; e += NT) {
         const int k = e - div_n(e, G.inv_n) * n;
         const T m = (T)sm.M[e];
-        sm.N[e] = m * __ldg(Sel<T>::invx(G) + k);  // N = M / x through the table of 1 / x
+        sm.NL[e].n = m * __ldg(Sel<T>::invx(G) + k);  // N = M / x through the table of 1 / x
         if (sizeof(T) != sizeof(double)) sm.Mt[e] = m;
       }
       __syncthreads();
@@ -743,7 +758,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
             int pos = j - s_lo[b];
             for (int b2 = 0; b2 < b; ++b2) pos += max(0, s_hi[b2] - s_lo[b2] + 1);
             sm.loff[pos] = (s_sp[b] * n + j) * n;
-            sm.lN[pos] = sm.N[e];
+            sm.lN[pos] = sm.NL[e].n;
           }
         }
         if (e >= NC && e < NCp) {
@@ -818,8 +833,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
             }
           }
           sm.loss[r] = R;
-          sm.lam[r] = (T)lamd;
-          sm.NL[r] = NLPair<T>{sm.N[r], (T)lamd};
+          sm.NL[r].l = (T)lamd;
+          if (sizeof(T) == sizeof(double)) sm.nlam[r] = sm.NL[r].n * (T)lamd;
         }
         if (tid == 0) s_task = 0;
         limited = __syncthreads_or(fired);
@@ -837,7 +852,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           int cnt = 0;
           for (int r0 = 0; r0 < E; r0 += 32) {
             const int r = r0 + lane;
-            const bool f = r < E && sm.lam[r] < T(1);
+            const bool f = r < E && sm.NL[r].l < T(1);
             const unsigned bal = __ballot_sync(0xffffffffu, f);
             if (f && FSBM_OK(t.chk, cnt + __popc(bal & ((1u << lane) - 1u)), E))
               sm.lim[cnt + __popc(bal & ((1u << lane) - 1u))] = r;
@@ -851,13 +866,15 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           if (q < L) {
             const int r = sm.lim[q];
             const int b = div_n(r, G.inv_n), j = r - b * n;
-            sm.llam[q] = sm.lam[r];
-            sm.lN[q] = sm.N[r];
+            sm.llam[q] = sm.NL[r].l;
+            sm.lN[q] = sm.NL[r].n;
             sm.loff[q] = (s_sp[b] * n + j) * n;
+            if (sizeof(T) == sizeof(double)) sm.lNl[q] = sm.nlam[r];
           } else {
             sm.llam[q] = T(1);
             sm.lN[q] = T(0);
             sm.loff[q] = 0;
+            if (sizeof(T) == sizeof(double)) sm.lNl[q] = T(0);
           }
         }
         __syncthreads();
@@ -869,7 +886,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           if (((i >= s_lo[a] && i <= s_hi[a]) || (i + 1 < n && i + 1 >= s_lo[a] && i + 1 <= s_hi[a])) &&
               (!FSBM_CHECKED_BUILD || (FSBM_OK(t.chk, s_sp[a], S) && FSBM_OK(t.chk, L, E + 1) &&
                                        FSBM_OK(t.chk, nch * E - 1, 2 * S * S * nmax)))) {
-            const T li0 = sm.lam[r], li1 = i + 1 < n ? sm.lam[r + 1] : T(1);
+            const T li0 = sm.NL[r].l, li1 = i + 1 < n ? sm.NL[r + 1].l : T(1);
             const T* __restrict__ Krow = Kr + (size_t)s_sp[a] * S * n * n + i;
             const T* __restrict__ Krowd = lev ? Krd + (size_t)s_sp[a] * S * n * n + i : nullptr;
             const int qa = ch * span, qb = min(Lp, qa + span);
@@ -896,10 +913,25 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
                     k1[u] = fma(wT, __ldg(Krowd + o[u] + 1), k1[u]);
                   }
                 }
+                if (sizeof(T) == sizeof(double)) {
+                  // FP64: (min(l_i, l_j) - l_i) N_j is 0 for l_j >= l_i and N_j l_j - l_i N_j
+                  // otherwise: one multiply-add on the listed N_j l_j and a select on the bit
+                  // patterns (non-negative ratios order like integers), two FP64 operations a term
+                  T nlj[8];
+                  lds8(sm.lNl + q, nlj);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                  p0[u & 3] = fma((min_nonneg(li0, lj[u]) - li0) * k0[u], nj[u], p0[u & 3]);
-                  p1[u & 3] = fma((min_nonneg(li1, lj[u]) - li1) * k1[u], nj[u], p1[u & 3]);
+                  for (int u = 0; u < 8; ++u) {
+                    const T t0 = lt_nonneg(lj[u], li0) ? fma(-li0, nj[u], nlj[u]) : T(0);
+                    const T t1 = lt_nonneg(lj[u], li1) ? fma(-li1, nj[u], nlj[u]) : T(0);
+                    p0[u & 3] = fma(k0[u], t0, p0[u & 3]);
+                    p1[u & 3] = fma(k1[u], t1, p1[u & 3]);
+                  }
+                } else {
+#pragma unroll
+                  for (int u = 0; u < 8; ++u) {
+                    p0[u & 3] = fma((min_nonneg(li0, lj[u]) - li0) * k0[u], nj[u], p0[u & 3]);
+                    p1[u & 3] = fma((min_nonneg(li1, lj[u]) - li1) * k1[u], nj[u], p1[u & 3]);
+                  }
                 }
               }
               acc0.add((p0[0] + p0[1]) + (p0[2] + p0[3]));
@@ -917,7 +949,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == sizeof(float) ? 2 : 1) k_coa
           if (i < s_lo[a] || i > s_hi[a]) continue;
           Sum tot = Num<T>::zero();
           for (int ch = 0; ch < nch; ++ch) Num<T>::add(tot, part[ch * E + r]);
-          const T li = sm.lam[r];
+          const T li = sm.NL[r].l;
           const double base = li < T(1) ? sm.M[r] : sm.loss[r];
           sm.loss[r] = base + dt * sm.M[r] * Num<T>::val(tot);
         }

@@ -468,8 +468,9 @@ fsbm_status fsbm_coal_init(const fsbm_coal_config* cfg, void* stream, fsbm_coal_
   }
   {
     // one point's spectra, sums and partial gains live in shared memory: refuse grids whose
-    // working set (about 8 (2 S + 2 S^2) n + (2 or 3) S n w bytes) exceeds the device's
-    // per-CTA limit (about 400 bins with 5 species on GB300)
+    // working set (about 8 (2 S + 2 S^2) n bytes plus 6 to 9 values of the form's width per
+    // species and bin) exceeds the device's per-CTA limit (on GB300: 297 bins with 5 species
+    // in FP64, 368 in FP32)
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess)
       return bail(FSBM_E_CUDA);
