@@ -129,7 +129,9 @@ typedef struct {
 typedef struct {                /* device pointers, caller-owned                          */
   void* spectra;                /* double (FSBM_FP64) or float (FSBM_FP32_SPLIT), packed:
                                    point p holds [stored species ascending][n_bins] at
-                                   element offset[p]; updated in place                     */
+                                   element offset[p]; updated in place. Must not be NULL
+                                   when n_points > 0, even if no point stores a species
+                                   (any valid device address then)                         */
   const int64_t* offset;        /* [n_points + 1] element offsets into spectra            */
   const uint8_t* grid_id;       /* [n_points]                                             */
   const uint8_t* species_mask;  /* [n_points] bit a set: species a stored                 */
@@ -273,16 +275,19 @@ typedef struct {
 FSBM_API fsbm_status fsbm_coal_step_wrf(fsbm_coal_ctx* ctx, const fsbm_wrf_state* state, double dt,
                                         int32_t n_steps);
 
-/* Time the collision kernel for each candidate CTA size (32, 64, 128, 256, 512 threads) on a
- * copy of the first 2^16 points of the given device state (all of it if smaller), stepping the
- * sample n_steps collision steps of dt seconds (the caller's own call shape: the limiter's
- * firing, and so the cost, depends on dt), and keep the fastest for later steps. The choice is
- * remembered for the process under a key of the device, precision, mode, kernel levels, bin
- * grids, species count, range threshold, dt, n_steps and the sample's mix of point classes
- * (grid and stored-species count, in eighths): a later call with the same key, from this or
- * another context, takes it without timing (fsbm_coal_get_stats: tune_cache_hit). The caller's
- * spectra are not modified. Synchronous; allocates a temporary copy of the sample. The paper
- * has no counterpart. */
+/* Time the collision kernel for each candidate CTA size (32, 64, 128, 256, 512 threads) and
+ * keep the fastest for later steps. The whole batch is classified and ordered as a step would
+ * order it; the timed sample is an even stride through that ordered list of active points,
+ * holding a fixed amount of work (every class in its share, wherever in the batch its points
+ * lie), stepped up to 4 collision steps of dt seconds (the caller's own step length: the
+ * limiter's firing, and so the cost, depends on dt). The choice is remembered for the process
+ * under a key of the device, precision, mode, kernel levels, bin grids, species count, range
+ * threshold, dt, n_steps, gain split and the batch's mix of active point classes (grid and
+ * stored-species count, in eighths): a later call with the same key, from this or another
+ * context, takes it without timing (fsbm_coal_get_stats: tune_cache_hit). A batch with no
+ * active point keeps the current CTA size. The caller's arrays are not modified: the tuner
+ * works on a temporary copy of the spectra and its own outputs. Synchronous; allocates that
+ * copy. The paper has no counterpart. */
 FSBM_API fsbm_status fsbm_coal_autotune_steps(fsbm_coal_ctx* ctx, const fsbm_coal_state* state, int64_t n_points,
                                               double dt, int32_t n_steps);
 
