@@ -16,10 +16,11 @@ Besides the headline number the line carries:
                (host->device and device->host copies inside the timed region);
   roofline     the collision kernel against the ALU roofline (pairs/s against the pipe
                rate divided by the algorithmic pipe operations per pair);
-  cpu_baseline the CPU oracle on a bounded sample of the same points, all host cores;
-  forms        the FP32 split form on the same domain (CUDA-graph replay), the same domain
-               through the WRF-layout entry point, the 264-bin 5-species stress points in
-               both forms, the ragged 33-264-bin batch, Bott's in-place (SWEEP) order, and
+  cpu_baseline the CPU oracle on a bounded sample of the same points, all host cores (N = 1);
+  forms        (N = 1) the FP32 split form on the same domain (CUDA-graph replay), the same
+               domain through the WRF-layout entry point and as replica streams, the 264-bin
+               5-species stress points in both forms, the ragged 2M-point 33-264-bin batch,
+               the Golovin configurations in both forms, Bott's in-place (SWEEP) order, and
                kernels at two pressure levels.
 
 --impl reference times the CPU oracle as the reference arm (bounded sample per step).
@@ -703,7 +704,9 @@ def main():
                          FP32_LANES, FP_OPS_PER_PAIR, MUFU_LANES, MUFU_OPS_PER_PAIR),
                      "clock_mhz": sm_mhz, "coal_ms_per_launch": coal_ms},
     }
-    if rank == 0 and not args.no_forms:
+    # the side forms and the CPU baseline are single-GPU measurements: at N > 1 they would hold
+    # the other GPUs idle for minutes, so they run at N = 1 only
+    if world == 1 and not args.no_forms:
         forms = {}
         other = pkg.FSBM_FP32_SPLIT if precision == pkg.FSBM_FP64 else pkg.FSBM_FP64
         r = run_form(pkg, torch, w, other, args.steps, 3, graph=(other == pkg.FSBM_FP32_SPLIT))
@@ -767,7 +770,7 @@ def main():
         fr["alu_frac"] = (pairs_per_active(w) * w.n_steps / (kms / 1e3)) / alu_peak_pairs(1 - precision, sm_mhz)
         line["forms"] = forms
         line["gpu_launches"] = (4 if world == 1 else 5) * args.steps
-    if rank == 0 and not args.no_cpu:
+    if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_sample_run(w)
     if rank == 0:
         print(json.dumps(line))
