@@ -9,7 +9,9 @@ workload's collision steps.
 Default workload (N = 1): the CONUS-12km-shaped domain, 425 x 300 x 50 points with 15 %
 cloudy (956,249 active points), 33 mass-doubling bins, 5 species, dt = 5 s x 10 collision
 steps per call, plain FP64 form. The spectra (1.26 GB) exceed L2, so no flush is needed
-between timed calls; the state keeps evolving from call to call, as in a model run.
+between timed calls. Every timed call steps the same batch: the spectra are restored from a
+copy of the starting state before each call, outside the timed events, so the rate does not
+drift with the number of calls (a batch left to evolve grows costlier per pair).
 
 Besides the headline number the line carries:
   e2e          the same metric through fsbm_coal_step_host with pinned host buffers
@@ -282,31 +284,48 @@ def synth_subset(w, idx):
 
 
 def time_steps(fc, ds, w, steps, warmup, stream, torch, barrier=None, shard=None):
-    """Warm-up calls, then ``steps`` timed calls between CUDA events on the context's stream.
-    ``shard`` = (rank, world) steps that rank's shard of the batch (fsbm_coal_step_shard)."""
+    """Warm-up calls, then ``steps`` timed calls, each between its own pair of CUDA events on the
+    context's stream. Every call steps the same batch: the spectra are restored from a device
+    copy of the starting state before each call, outside the events (a call updates them in
+    place, and a batch left to evolve over many calls is no longer the configured workload: it
+    grows costlier per pair). ``shard`` = (rank, world) steps that rank's shard of the batch
+    (fsbm_coal_step_shard)."""
     def one():
         if shard and shard[1] > 1:
             fc.step_shard(ds, w.dt, w.n_steps, shard[0], shard[1])
         else:
             fc.step(ds, w.dt, w.n_steps)
 
+    torch.cuda.synchronize()
+    init = ds.t["spectra"].clone()
+    torch.cuda.synchronize()
+
+    def restore():
+        with torch.cuda.stream(stream):
+            ds.t["spectra"].copy_(init)
+
     for _ in range(warmup):
+        restore()
         one()
     torch.cuda.synchronize()
     fc.stats()  # reset the timing totals
     if barrier:
         barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        restore()
+        e0.record(stream)
         one()
-    e1.record(stream)
+        e1.record(stream)
     torch.cuda.synchronize()
     if barrier:
         barrier()
-    ms = e0.elapsed_time(e1)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    with torch.cuda.stream(stream):
+        ds.t["spectra"].copy_(init)  # leave the batch as it came
+    torch.cuda.synchronize()
+    del init
     return ms, fc.stats()
 
 
@@ -353,17 +372,27 @@ def run_wrf_form(pkg, torch, w, precision, steps, warmup):
         st = torch.zeros(w.n_points, dtype=torch.int32, device=dev)
         mem = (1, im, 1, km, 1, jm)
         fc.set_timing(False)
+        init = [f.clone() for f in ff]  # every call steps the same fields (restored outside the events)
+        torch.cuda.synchronize()
+
+        def restore():
+            with torch.cuda.stream(fc.stream):
+                for f, f0 in zip(ff, init):
+                    f.copy_(f0)
+
         for _ in range(warmup):
+            restore()
             fc.step_wrf(ff, mem, mem, w.dt, w.n_steps, temperature=temp, predicate=pred, status=st)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(fc.stream)
-        for _ in range(steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            restore()
+            e0.record(fc.stream)
             fc.step_wrf(ff, mem, mem, w.dt, w.n_steps, temperature=temp, predicate=pred, status=st)
-        e1.record(fc.stream)
+            e1.record(fc.stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        del init
         n_active = int(((st == 0) | (st == 1)).sum().item())
     return dict(value=n_active * w.n_steps * steps / (ms / 1e3), ms_per_step=ms / steps, n_active=n_active,
                 points=w.n_points, layout="[species][bin][j][k][i], i fastest; tile = whole domain")
@@ -394,20 +423,31 @@ def run_replicas_form(pkg, torch, w, precision, R, steps, warmup):
     with pkg.FsbmCoal(w.cfg(), precision=precision) as fc:
         for label, ctxs, parts in (("batched", [fc], [w]), ("replicas", [fc.clone() for _ in range(R)], slabs)):
             dss = [c.upload(p.state(copy=False)) for c, p in zip(ctxs, parts)]
+            inits = [d.t["spectra"].clone() for d in dss]  # every iteration steps the same batch
             for c in ctxs:
                 c.set_block(256)
+
+            def restore():
+                torch.cuda.synchronize()
+                for d, d0 in zip(dss, inits):
+                    d.t["spectra"].copy_(d0)
+                torch.cuda.synchronize()
+
             for _ in range(warmup):
+                restore()
                 for c, d, p in zip(ctxs, dss, parts):
                     c.step(d, p.dt, p.n_steps)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
+            wall = 0.0
             for _ in range(steps):
+                restore()
+                t0 = time.perf_counter()
                 for c, d, p in zip(ctxs, dss, parts):
                     c.step(d, p.dt, p.n_steps)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
+                torch.cuda.synchronize()
+                wall += time.perf_counter() - t0
             n_act = sum(int(c.stats()["n_active"]) for c in ctxs)
-            out[label] = n_act * w.n_steps * steps / (t1 - t0)
+            out[label] = n_act * w.n_steps * steps / wall
+            del inits
             del dss
             if label == "replicas":
                 for c in ctxs:
@@ -640,11 +680,13 @@ def main():
         out_bytes = hw.n_points * (8 + 8 + 4)
         h2d = sum(a.nbytes for a in pinned.values())
         d2h = pinned["spectra"].nbytes + out_bytes
+        spec0 = pinned["spectra"].copy()  # every call steps the same batch (restored outside the timer)
         fc.step_host(pinned, w.dt, w.n_steps)  # first call sizes the device mirrors
         barrier()
         e2e_steps = min(args.steps, 5)  # each call copies the whole batch in and out (synchronous)
         e2e_calls = []
         for _ in range(e2e_steps):
+            np.copyto(pinned["spectra"], spec0)
             t0 = time.perf_counter()
             fc.step_host(pinned, w.dt, w.n_steps)
             e2e_calls.append(time.perf_counter() - t0)
